@@ -1,0 +1,338 @@
+"""Checks that pin the FP64 oracle to facts fixed outside itself.
+
+Each check raises AssertionError on a mismatch. They are plain functions so
+that ``test_oracle_pins.py`` runs them against the real oracle and
+``test_oracle_mutants.py`` runs them against oracle builds with a planted
+mistake (each mutant must fail at least one check).
+
+Sources of truth:
+  - hand traces derived on paper from §III.A-C (``golden/*.txt``);
+  - closed forms of the update under a constant input (geometric series);
+  - invariants stated in §III.A (weights positive, summing to one) and
+    implied by the method (sorted rank keys, variance floor, |cpt| <= 3);
+  - brute force: all permutations for the rank order (exact rational keys),
+    exact rational prefix sums for B;
+  - a special case that reduces to a library routine (scipy's binary
+    opening for the 3x3 clean-up).
+"""
+from __future__ import annotations
+
+import itertools
+import os
+import random
+from fractions import Fraction
+
+import numpy as np
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _frac(s: str) -> float:
+    return float(Fraction(s))
+
+
+# ---------------------------------------------------------------- hand traces
+def load_hand_trace(name="hand_trace_2x2.txt"):
+    params, frames, outs, states = {}, {}, {}, {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            tok = line.split()
+            if tok[0] == "param":
+                params[tok[1]] = Fraction(tok[2])
+            elif tok[0] == "frame":
+                t = int(tok[1]); i = tok.index("depth")
+                frames[t] = ([int(v) for v in tok[3:i]], [int(v) for v in tok[i + 1:]])
+            elif tok[0] == "out":
+                outs[(int(tok[1]), tok[2])] = [int(v) for v in tok[3:]]
+            elif tok[0] == "state":
+                states[(int(tok[1]), tok[2], tok[3])] = [_frac(v) for v in tok[4:]]
+    return params, frames, outs, states
+
+
+def check_hand_trace():
+    params, frames, outs, states = load_hand_trace()
+    M = int(params["M"])
+    g = O.OracleGMM(2, 2, M, float(params["alpha"]), float(params["k"]), float(params["T"]),
+                    float(params["init_var"]), float(params["init_w"]),
+                    v_min_c=float(params["v_min"]), v_min_d=float(params["v_min"]))
+    for t in sorted(frames):
+        grey, dep = frames[t]
+        rgb = np.repeat(np.array(grey, np.uint8).reshape(2, 2, 1), 3, axis=2)
+        out = g.tick(rgb, np.array(dep, np.uint16).reshape(2, 2))
+        for name in ("fg_rgb", "fg_d", "fused"):
+            exp = outs.get((t, name))
+            if exp is not None:
+                got = out[name].reshape(-1).tolist()
+                assert got == exp, f"frame {t} {name}: {got} != {exp}"
+        exp = outs.get((t, "fusion_byte"))
+        if exp is not None:
+            got = g.fusion_bytes().reshape(-1).tolist()
+            assert got == exp, f"frame {t} fusion byte: {got} != {exp}"
+    for (p, stream, field), exp in states.items():
+        if stream == "colour":
+            got = {"w": g.wc[p], "mu": g.muc[p][:, 0], "v": g.vc[p]}[field]
+            if field == "mu":  # grey input: all three channels equal
+                assert np.array_equal(g.muc[p][:, 0], g.muc[p][:, 1])
+                assert np.array_equal(g.muc[p][:, 0], g.muc[p][:, 2])
+        else:
+            got = {"w": g.wd[p], "mu": g.mud[p], "v": g.vd[p]}[field]
+        assert np.allclose(got, exp, rtol=1e-7, atol=1e-12), f"pixel {p} {stream} {field}: {got} != {exp}"
+
+
+def load_list1_traces(name="list1_traces.txt"):
+    traces, cur = [], None
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            tok = line.split()
+            if tok[0] == "trace":
+                cur = {"name": tok[1], "F0": int(tok[2]), "steps": []}
+            elif tok[0] == "step":
+                cur["steps"].append((int(tok[1]), int(tok[2]), int(tok[4]), int(tok[5])))
+            elif tok[0] == "end":
+                traces.append(cur)
+    return traces
+
+
+def check_list1_traces():
+    for tr in load_list1_traces():
+        F, cpt = tr["F0"], 0
+        for i, (r, d, eF, ec) in enumerate(tr["steps"]):
+            F, cpt = O.fuse(r, d, F, cpt)
+            assert (F, cpt) == (eF, ec), f"{tr['name']} step {i}: {(F, cpt)} != {(eF, ec)}"
+
+
+def check_list1_properties(max_len=7):
+    """Over every (rgb, d) sequence up to max_len from both labels: the
+    counter stays in [-3, 3]; agreement sets the label to the common answer
+    and clears the counter; on disagreement the label can change only on a
+    step that starts with |cpt| = 3, and then it takes the answer of the
+    stream the sign names (+3 colour, -3 depth)."""
+    pairs = [(0, 0), (0, 1), (1, 0), (1, 1)]
+    for F0 in (0, 1):
+        for L in range(1, max_len + 1):
+            for seq in itertools.product(range(4), repeat=L):
+                F, cpt = F0, 0
+                for s in seq:
+                    r, d = pairs[s]
+                    F1, c1 = O.fuse(r, d, F, cpt)
+                    assert -3 <= c1 <= 3
+                    if r == d:
+                        assert (F1, c1) == (d, 0)
+                    elif cpt == 3:
+                        assert (F1, c1) == (r, 0)
+                    elif cpt == -3:
+                        assert (F1, c1) == (d, 0)
+                    else:
+                        assert F1 == F and abs(c1 - cpt) == 1
+                    F, cpt = F1, c1
+
+
+# ---------------------------------------------------------------- closed forms
+def check_closed_form_constant_input(D=3, steps=200):
+    """A component that matches a constant input c keeps matching, and
+    mu_t = c + (mu_0 - c) r^t, v_t = r^t [v_0 + |mu_0 - c|^2 r (1 - r^t)],
+    w_match(t) = 1 - (1 - w_0) r^t, w_other(t) = w_other(0) r^t, r = 1 - alpha
+    (geometric series of the update; valid while v stays above v_min)."""
+    alpha = 0.015625  # exact in float32
+    r = 1.0 - alpha
+    M = 4
+    c = np.array([120.0, 64.0, 33.0][:D])
+    mu0 = c + np.array([3.0, -2.0, 1.5][:D])
+    v0 = 64.0
+    e = float(np.sum((mu0 - c) ** 2))
+    prm = O.stream_params(alpha, 2.5, 0.7, 900.0, 0.05, v_min=1e-3)
+    w = np.array([0.55, 0.25, 0.15, 0.05])
+    mu = np.zeros((M, D)); mu[0] = mu0
+    for i in range(1, M):
+        mu[i] = c + 500.0 + 40.0 * i
+    v = np.array([v0, 400.0, 900.0, 1600.0])
+    w_other0 = w[1:].copy()
+    for t in range(1, steps + 1):
+        fg, info = O.stream_step(prm, w, mu, v, c)
+        assert info[0] == 0 and info[2] == 0 and fg == 0, f"t={t}: info {info}"
+        rt = r ** t
+        assert np.allclose(mu[0], c + (mu0 - c) * rt, rtol=1e-12, atol=1e-11)
+        assert np.isclose(v[0], rt * (v0 + e * r * (1.0 - rt)), rtol=1e-11)
+        assert np.isclose(w[0], 1.0 - (1.0 - 0.55) * rt, rtol=1e-12)
+        assert np.allclose(w[1:], w_other0 * rt, rtol=1e-11)
+
+
+def check_closed_form_depth():
+    check_closed_form_constant_input(D=1, steps=150)
+
+
+# ---------------------------------------------------------------- invariants
+def check_invariants_random(seed=3, pixels=40, steps=120):
+    rng = random.Random(seed)
+    for p in range(pixels):
+        M = 3 + p % 3
+        D = 3 if p % 2 == 0 else 1
+        alpha = rng.choice([0.01, 0.05, 0.2])
+        v_min = rng.choice([1.0, 4.0])
+        prm = O.stream_params(alpha, 2.5, rng.choice([0.5, 0.7, 0.9]), 225.0, 0.05, v_min=v_min)
+        base = np.array([rng.uniform(20, 230) for _ in range(D)])
+        w, mu, v = O.stream_init(M, D, 225.0, base)
+        for t in range(steps):
+            u = rng.random()
+            if u < 0.7:
+                x = base + np.array([rng.gauss(0, 3) for _ in range(D)])
+            elif u < 0.85:
+                x = base + 60.0
+            else:
+                x = np.array([rng.uniform(0, 255) for _ in range(D)])
+            fg, info = O.stream_step(prm, w, mu, v, x)
+            assert np.all(w > 0), w
+            assert abs(w.sum() - 1.0) <= 1e-12, w.sum()
+            assert np.all(v >= np.float32(v_min)), v
+            key = w / np.sqrt(v)
+            assert np.all(np.diff(key) <= 0), key
+            j_before, B, rank_j, near = info
+            assert 1 <= B <= M and 0 <= rank_j < M
+            if j_before < 0:
+                assert fg == 1
+                assert np.array_equal(mu[rank_j], x) and v[rank_j] == np.float32(225.0)
+            else:
+                assert fg == int(rank_j >= B)
+
+
+def check_special_case_T_near_one(seed=5):
+    """T just below 1: the background set is every component, so any match
+    is background."""
+    rng = random.Random(seed)
+    T = float(np.nextafter(np.float32(1.0), np.float32(0.0)))
+    prm = O.stream_params(0.05, 2.5, T, 100.0, 0.3)
+    for _ in range(20):
+        w, mu, v = O.stream_init(5, 1, 100.0, [1000.0])
+        for t in range(60):
+            x = [1000.0 + (rng.gauss(0, 4) if rng.random() < 0.8 else rng.uniform(-800, 800))]
+            fg, info = O.stream_step(prm, w, mu, v, x)
+            if info[0] >= 0:
+                assert fg == 0 and info[1] == 5, info
+
+
+def check_first_match_wins():
+    """Two components both within k sigma of the sample: the better ranked
+    one (stored first) is the one that matches and gets updated (§III.A,
+    test against the most weighted distribution first)."""
+    prm = O.stream_params(0.25, 2.5, 0.7, 100.0, 0.05)
+    w = np.array([0.5, 0.3, 0.2]); mu = np.array([[100.0], [104.0], [300.0]]); v = np.array([16.0, 16.0, 16.0])
+    fg, info = O.stream_step(prm, w, mu, v, [103.0])
+    assert info[0] == 0 and fg == 0
+    assert np.isclose(mu[0, 0], 0.75 * 100.0 + 0.25 * 103.0) and mu[1, 0] == 104.0
+    # strict threshold: d^2 == k^2 v exactly is not a match
+    w = np.array([0.5, 0.3, 0.2]); mu = np.array([[100.0], [200.0], [300.0]]); v = np.array([16.0, 16.0, 16.0])
+    fg, info = O.stream_step(prm, w, mu, v, [110.0])  # d^2 = 100 = 6.25 * 16
+    assert info[0] == -1 and fg == 1
+    # the bound is k standard deviations: d^2 = 79.21 lies between k v and k^2 v
+    w = np.array([0.5, 0.3, 0.2]); mu = np.array([[100.0], [200.0], [300.0]]); v = np.array([16.0, 16.0, 16.0])
+    fg, info = O.stream_step(prm, w, mu, v, [108.9])
+    assert info[0] == 0 and fg == 0
+
+
+# ---------------------------------------------------------------- brute force
+def _brute_stable_rank(w, v):
+    """Unique permutation with non-increasing key (compared exactly through
+    w^2 / v as rationals) and equal keys in stored order."""
+    M = len(w)
+    k2 = [Fraction(w[i]) ** 2 / Fraction(v[i]) for i in range(M)]
+    found = []
+    for perm in itertools.permutations(range(M)):
+        ok = True
+        for a in range(M - 1):
+            i, j = perm[a], perm[a + 1]
+            if k2[i] < k2[j] or (k2[i] == k2[j] and i > j):
+                ok = False
+                break
+        if ok:
+            found.append(list(perm))
+    assert len(found) == 1
+    return found[0]
+
+
+def check_rank_order_bruteforce():
+    # every tie pattern: keys drawn from M levels, v in {1, 4, 16} so sqrt is exact
+    for M in (3, 4, 5):
+        levels = [Fraction(n, 64) for n in (3, 5, 7, 11, 13)][:M]
+        vs = [1.0, 4.0, 16.0]
+        for pat in itertools.product(range(M), repeat=M):
+            v = np.array([vs[(i * 7 + pat[i]) % 3] for i in range(M)])
+            w = np.array([float(levels[pat[i]]) * np.sqrt(v[i]) for i in range(M)])
+            got = O.rank_order(w, v).tolist()
+            exp = _brute_stable_rank(w, v)
+            assert got == exp, f"pattern {pat}: {got} != {exp}"
+    rng = random.Random(11)
+    for _ in range(300):
+        M = rng.choice([3, 4, 5])
+        w = np.array([rng.uniform(0.01, 1.0) for _ in range(M)])
+        v = np.array([rng.uniform(1.0, 400.0) for _ in range(M)])
+        assert O.rank_order(w, v).tolist() == _brute_stable_rank(w, v)
+
+
+def check_background_count_exact():
+    # exact ties with dyadic weights: a prefix equal to T is not above it
+    assert O.background_count(np.array([0.25, 0.25, 0.5]), 0.5) == 3
+    assert O.background_count(np.array([0.5, 0.25, 0.25]), 0.5) == 2
+    assert O.background_count(np.array([0.75, 0.125, 0.0625, 0.0625]), 0.75) == 2
+    assert O.background_count(np.array([0.125, 0.125, 0.25, 0.5]), 0.999) == 4
+    rng = random.Random(17)
+    for _ in range(500):
+        M = rng.choice([3, 4, 5])
+        raw = [rng.randint(1, 1000) for _ in range(M)]
+        tot = sum(raw)
+        w = [Fraction(r, tot) for r in raw]
+        T = Fraction(rng.randint(1, 999), 1000)
+        # exact: first prefix strictly above T
+        B = next((b + 1 for b in range(M) if sum(w[:b + 1]) > T), M)
+        wf = np.array([float(x) for x in w])
+        prefix = np.cumsum([float(x) for x in w])
+        if np.any(np.abs(prefix - float(T)) < 1e-12):
+            continue  # float rounding can legitimately decide an exact tie
+        assert O.background_count(wf, float(T)) == B
+
+
+def check_morph_open_against_scipy():
+    import scipy.ndimage as ndi
+    rng = np.random.default_rng(2)
+    for H, W in ((1, 1), (1, 7), (5, 1), (9, 13), (32, 40)):
+        for p in (0.3, 0.7, 0.95):
+            m = (rng.random((H, W)) < p).astype(np.uint8)
+            exp = ndi.binary_opening(m, structure=np.ones((3, 3)), border_value=0).astype(np.uint8)
+            assert np.array_equal(O.morph_open3(m), exp)
+    # a lone pixel vanishes, a 3x3 block away from the border survives
+    m = np.zeros((7, 7), np.uint8); m[1, 1] = 1; m[3:6, 3:6] = 1
+    out = O.morph_open3(m)
+    assert out[1, 1] == 0 and out[3:6, 3:6].all() and out.sum() == 9
+
+
+def check_depth_invalid_and_late_start():
+    """Zero depth leaves the depth model untouched and copies the colour
+    answer; the depth model starts at the first non-zero reading."""
+    g = O.OracleGMM(1, 2, 3, 0.1, 2.5, 0.6, 100.0, 0.05)
+    rgb = np.full((1, 2, 3), 90, np.uint8)
+    g.tick(rgb, np.array([[0, 1200]], np.uint16))
+    assert g.dinit.tolist() == [0, 1] and np.all(g.wd[0] == 0)
+    rgb2 = rgb.copy(); rgb2[0, :, :] = 250  # colour miss everywhere
+    out = g.tick(rgb2, np.array([[0, 1200]], np.uint16))
+    assert out["fg_rgb"].tolist() == [[1, 1]]
+    assert out["fg_d"].tolist() == [[1, 0]]   # invalid copies colour; valid matches
+    assert np.all(g.wd[0] == 0) and g.dinit[0] == 0
+    out = g.tick(rgb, np.array([[1500, 1200]], np.uint16))
+    assert g.dinit[0] == 1 and out["fg_d"][0, 0] == 0
+    assert np.allclose(g.mud[0], 1500.0) and np.allclose(g.wd[0], 1 / 3)
+
+
+ALL_CHECKS = [
+    check_hand_trace, check_list1_traces, check_list1_properties,
+    check_closed_form_constant_input, check_closed_form_depth,
+    check_invariants_random, check_special_case_T_near_one, check_first_match_wins,
+    check_rank_order_bruteforce, check_background_count_exact,
+    check_morph_open_against_scipy, check_depth_invalid_and_late_start,
+]

@@ -1,0 +1,73 @@
+"""Plant plausible mistakes in copies of the oracle and check that the pins
+catch every one. Each mutant is compiled from a patched copy of
+``oracle/gmm_oracle.c`` into a temporary directory; the real oracle is never
+modified."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import oracle as O
+import oracle_pins as P
+
+SRC = os.path.join(os.path.dirname(O.__file__), "gmm_oracle.c")
+
+MUTANTS = {
+    "distance_sign": ("double diff = x[c] - mu[i * D + c];", "double diff = x[c] + mu[i * D + c];"),
+    "match_not_strict": ("if (d2 < lim)", "if (d2 <= lim)"),
+    "k_not_squared": ("double lim = k * k * v[i];", "double lim = k * v[i];"),
+    "no_renormalise": ("w[i] = w[i] / s;", "w[i] = w[i];"),
+    "no_match_gain": ("w[j] = w[j] + alpha;", "w[j] = w[j];"),
+    "no_decay": ("w[i] = (1.0 - alpha) * w[i];", "w[i] = w[i];"),
+    "replace_best": ("j = M - 1;", "j = 0;"),
+    "sort_ascending": ("key[perm[r - 1]] < key[p]", "key[perm[r - 1]] > key[p]"),
+    "sort_unstable": ("key[perm[r - 1]] < key[p]", "key[perm[r - 1]] <= key[p]"),
+    "key_w_over_v": ("return w / sqrt(v);", "return w / v;"),
+    "payload_not_permuted": ("tmu[r * D + c] = mu[p * D + c];", "tmu[r * D + c] = mu[r * D + c];"),
+    "B_not_strict": ("if (s > T)", "if (s >= T)"),
+    "fg_rank_off_by_one": ("(rank_j >= B)", "(rank_j > B)"),
+    "variance_old_mean": ("double diff = x[c] - mu[j * D + c];",
+                          "double diff = (x[c] - mu[j * D + c]) / (1.0 - alpha);"),
+    "variance_no_decay": ("double vn = (1.0 - alpha) * v[j] + alpha * d2;", "double vn = v[j] + alpha * d2;"),
+    "init_weight_unnormalised": ("w[i] = 1.0 / (double)M;", "w[i] = 1.0;"),
+    "list1_three_frames": ("if (*cpt == 3)", "if (*cpt == 2)"),
+    "list1_plus3_to_depth": ("*F = f_rgb;", "*F = f_d;"),
+    "list1_counter_direction": ("*cpt = *cpt + 1;", "*cpt = *cpt - 1;"),
+    "invalid_depth_background": ("fdp = fc;", "fdp = 0;"),
+    "morph_outside_one": ("int val = 0;", "int val = 1;"),
+}
+
+
+@pytest.fixture
+def swap_oracle_lib():
+    saved = O._lib
+
+    def install(lib):
+        O._declare(lib)
+        O._lib = lib
+
+    yield install
+    O._lib = saved
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path, swap_oracle_lib):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mutated = src.replace(old, new, 1)
+    c_path = tmp_path / "mutant.c"
+    c_path.write_text(mutated)
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(so),
+                    str(c_path), "-lm"], check=True)
+    swap_oracle_lib(ctypes.CDLL(str(so)))
+    failed = []
+    for check in P.ALL_CHECKS:
+        try:
+            check()
+        except AssertionError:
+            failed.append(check.__name__)
+            break
+    assert failed, f"no pin caught mutant {name}"

@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the RGB-D Gaussian-mixture background subtraction
+and fusion tick on GB300.
+
+One step = one tick of the whole path (colour mixture, depth mixture, List-1
+fusion, bit-packed mask) over one frame of the workload. The metric is
+Mpixel-frames/s; the JSON line also carries the HBM roofline fraction of the
+tick kernel, per-tick latency percentiles, an end-to-end figure through the
+host-memory C-ABI path, and the FP64 oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c1]
+  python bench.py --impl reference ...   # the oracle arm, on host cores
+
+Frames are synthetic (seeded generator standing in for Kinect captures) and
+resident in device memory before the timed region. Under torchrun every rank
+runs its own camera (weak scaling, no data-path collective); the timed region
+is bracketed by a barrier and a device synchronisation and the slowest
+rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PARAMS = dict(alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0, init_w=0.05)
+WORKLOADS = {
+    "c0": dict(name="single camera 640x480, M=3, FP32 state, 100-frame sequence",
+               H=480, W=640, M=3, kind=0, frames=100, prec=0),
+    "c1": dict(name="single camera 1920x1080, M=5, FP32 state, 300-frame sequence",
+               H=1080, W=1920, M=5, kind=1, frames=300, prec=0),
+}
+METRIC = "Mpixel-frames/s (RGB+depth GMM+fusion)"
+UNIT = "Mpixel-frames/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 129 * 1024 * 1024
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gmm_tick_f32_m5_1920x1080.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2110_14934_gb300", "csrc", f)
+                  for f in ("gmm_device.cuh", "gmm_kernels.cu")]
+
+
+def bytes_per_pixel(M: int, prec: int) -> float:
+    """Algorithmic bytes per pixel and tick: state read + written (8 values
+    per component: 4 bytes each in FP32, 2 in FP16/BF16), RGB (3) + depth (2)
+    read, the List-1 byte read and written (2), one mask bit (1/8)."""
+    per_comp = 64 if prec == 0 else 32
+    return per_comp * M + 3 + 2 + 2 + 0.125
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    if workload != "c1" or not os.path.exists(TRAFFIC_FILE):
+        return None
+    text = open(TRAFFIC_FILE).read()
+    m = re.search(r"traffic_bytes_per_launch\s*=\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_sha256_16\s*=\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Each rank owns its own camera: an independent seeded sequence."""
+    return base + 7919 * rank
+
+
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max of a float over ranks (the slowest rank's time); identity at N=1."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a window."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.samples = []
+        self.t0 = self.t1 = None
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(gpu_index), "-lms", str(period_ms)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
+
+    def wait_first(self, timeout=10.0):
+        t = time.time()
+        while self.proc and not self.samples and time.time() - t < timeout:
+            time.sleep(0.05)
+
+    def start(self):
+        self.t0 = time.perf_counter()
+
+    def stop(self):
+        self.t1 = time.perf_counter()
+        time.sleep(0.12)  # let the sample straddling the end arrive
+
+    def close(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or self.t0 is None:
+            return None
+        win = [s for (t, s) in self.samples if self.t0 <= t <= self.t1]
+        window = "timed"
+        if not win:  # region shorter than the sampling period: nearest sample
+            near = sorted(self.samples, key=lambda ts: abs(ts[0] - self.t1))[:1]
+            win = [s for (_, s) in near]
+            window = "nearest"
+        sm, mx, reasons = [], [], set()
+        for s in win:
+            try:
+                sm.append(float(s[1]))
+                mx.append(float(s[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(self.REASONS, s[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "window": window}
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_rate(wl: dict, frames: int, rows: int, seed: int):
+    """Time the FP64 oracle on `rows` rows (a horizontal band through the
+    middle) of the first `frames` frames of the workload. Returns
+    (Mpixel-frames/s, seconds, sample description). Single thread."""
+    import oracle as O
+    import synth
+    H, W, M = wl["H"], wl["W"], wl["M"]
+    rows = max(1, min(rows, H))
+    y0 = (H - rows) // 2
+    s = synth.scene(seed, H, W, wl["kind"])
+    rgb, dep, _ = synth.rows_host(s, 0, frames, y0, rows)
+    g = O.OracleGMM(rows, W, M, **{k: PARAMS[k] for k in ("alpha", "match_k", "bg_T", "init_var", "init_w")})
+    g.tick(rgb[0], dep[0])  # first frame initialises; not timed
+    t = time.perf_counter()
+    for f in range(1, frames):
+        g.tick(rgb[f], dep[f])
+    dt = time.perf_counter() - t
+    px = (frames - 1) * rows * W
+    return px / dt / 1e6, dt, f"frames 1-{frames - 1} of the sequence, rows {y0}-{y0 + rows - 1} " \
+                              f"({rows}x{W} px per frame), FP64, 1 thread"
+
+
+def run_reference(args, wl):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    # size each step's sample so that warmup + steps take about a minute
+    probe_rate, _, _ = oracle_rate(wl, 3, 16, 1)
+    target_s = float(os.environ.get("GMM_REFERENCE_SECONDS", "60"))
+    steps = args.steps + args.warmup
+    rows = int(max(1, min(wl["H"], target_s * probe_rate * 1e6 / max(steps, 1) / wl["W"])))
+    import oracle as O
+    import synth
+    H, W, M = wl["H"], wl["W"], wl["M"]
+    y0 = (H - rows) // 2
+    s = synth.scene(1, H, W, wl["kind"])
+    nf = min(wl["frames"], steps + 1)
+    rgb, dep, _ = synth.rows_host(s, 0, nf, y0, rows)
+    g = O.OracleGMM(rows, W, M, **PARAMS)
+    for k in range(args.warmup):
+        g.tick(rgb[k % nf], dep[k % nf])
+    t = time.perf_counter()
+    for k in range(args.steps):
+        f = (args.warmup + k) % nf
+        g.tick(rgb[f], dep[f])
+    dt = time.perf_counter() - t
+    value = args.steps * rows * W / dt / 1e6
+    sample = f"each step: rows {y0}-{y0 + rows - 1} ({rows}x{W} px) of one frame, FP64, 1 thread"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(args.workload, wl, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(key, wl, world):
+    state_mb = wl["H"] * wl["W"] * wl["M"] * (32 if wl["prec"] == 0 else 16) / 1e6
+    return {"workload": f"{key}: {wl['name']}", "H": wl["H"], "W": wl["W"], "M": wl["M"],
+            "state": "f32" if wl["prec"] == 0 else "f16/bf16",
+            "alpha": PARAMS["alpha"], "k": PARAMS["match_k"], "T": PARAMS["bg_T"],
+            "cameras_per_gpu": 1, "parallelism": f"camera-sharded x{world}",
+            "l2": f"state {state_mb:.0f} MB per camera vs L2 129 MB: "
+                  + ("inputs larger than L2 between iterations" if state_mb * 1e6 > L2_BYTES
+                     else "state may stay L2-resident")}
+
+
+# ---------------------------------------------------------------- our arm
+def run_gmm(args, wl):
+    import torch
+    import paper_2110_14934_gb300 as G
+    import synth
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    H, W, M, prec = wl["H"], wl["W"], wl["M"], wl["prec"]
+    nf = min(wl["frames"], args.frames) if args.frames > 0 else wl["frames"]
+    scene = synth.scene(rank_seed(1, rank), H, W, wl["kind"])
+    rgb_d, dep_d, _ = synth.frames_device(scene, 0, nf, device=dev, with_gt=False)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    g = G.GMM(H, W, M, precision=prec, device=dev, **PARAMS)
+    mask = g.new_mask()
+    K, Wm = args.steps, args.warmup
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.wait_first()
+    for k in range(Wm):
+        g.apply(rgb_d[k % nf], dep_d[k % nf], mask, stream=stream)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    barrier(world, dev)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    for k in range(K):
+        f = (Wm + k) % nf
+        starts[k].record(stream)
+        g.apply(rgb_d[f], dep_d[f], mask, stream=stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier(world, dev)
+    if clocks:
+        clocks.stop()
+    tick_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = starts[0].elapsed_time(ends[-1])
+    total_ms = reduce_max(total_ms, world, dev)
+    value = world * K * H * W / (total_ms / 1e3) / 1e6
+
+    # roofline of the tick kernel (the only kernel in the timed region)
+    bpp = bytes_per_pixel(M, prec)
+    avg_kernel_s = statistics.fmean(tick_ms) / 1e3
+    achieved = H * W * bpp / avg_kernel_s / 1e9
+    peak, peak_src = measured_hbm_peak()
+    traffic = recorded_traffic(args.workload)
+
+    # end to end through the host-memory C-ABI path (pipelined, Fig. 4(a))
+    e2e = run_e2e(G, torch, g_args=(H, W, M, prec), frames=(rgb_d, dep_d), dev=dev,
+                  steps=args.e2e_steps or K, warmup=Wm, world=world)
+    del rgb_d, dep_d
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_frames > 0:
+        v, secs, sample = oracle_rate(wl, args.cpu_frames, args.cpu_rows or H, rank_seed(1, 0))
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": secs}
+    if clocks:
+        clk = clocks.summary()
+        clocks.close()
+    if rank == 0:
+        tick_sorted = sorted(tick_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(args.workload, wl, world),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_src, "algorithmic_bytes_per_px": bpp,
+                         "kernel": f"k_tick<M={M},{'f32' if prec == 0 else 'f16'}>"},
+            "latency_ms": {"tick_p50": pct(tick_sorted, 50), "tick_p99": pct(tick_sorted, 99),
+                           "e2e_p50": e2e["lat_p50"], "e2e_p99": e2e["lat_p99"]},
+            "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
+                    "d2h_bytes_per_step": e2e["d2h"], "path": "gmm_pipe_submit/gmm_pipe_wait, "
+                    "pinned host frames, 3 frames in flight"},
+            "cpu_baseline": cpu,
+            "gpu_launches": K,
+            "clocks": clk if clocks else None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def pct(sorted_vals, p):
+    if not sorted_vals:
+        return None
+    i = min(len(sorted_vals) - 1, max(0, int(round(p / 100.0 * (len(sorted_vals) - 1)))))
+    return sorted_vals[i]
+
+
+def run_e2e(G, torch, g_args, frames, dev, steps, warmup, world):
+    """Host frames (pinned) -> C-ABI pipelined path -> host masks. Timed from
+    the first submit to the last mask in host memory; per-frame latency from a
+    separate unpipelined pass (submit, wait)."""
+    H, W, M, prec = g_args
+    rgb_d, dep_d = frames
+    n_host = min(32, rgb_d.shape[0])
+    rgb_h = torch.empty((n_host, H, W, 3), dtype=torch.uint8).pin_memory()
+    dep_h = torch.empty((n_host, H, W), dtype=torch.int16).pin_memory()
+    rgb_h.copy_(rgb_d[:n_host])
+    dep_h.copy_(dep_d[:n_host])
+    ring = 8
+    masks = torch.empty((ring, H, G.mask_words_per_row(W)), dtype=torch.int32).pin_memory()
+    g = G.GMM(H, W, M, precision=prec, device=dev, **PARAMS)
+    g.set_stream(torch.cuda.current_stream(dev))
+    pending = []
+
+    def submit(k):
+        pending.append(g.pipe_submit(rgb_h[k % n_host], dep_h[k % n_host], masks[k % ring]))
+        if len(pending) >= G.PIPE_DEPTH:
+            g.pipe_wait(pending.pop(0), 60000)
+
+    for k in range(warmup):
+        submit(k)
+    while pending:
+        g.pipe_wait(pending.pop(0), 60000)
+    barrier(world, dev)
+    t = time.perf_counter()
+    for k in range(steps):
+        submit(warmup + k)
+    while pending:
+        g.pipe_wait(pending.pop(0), 60000)
+    dt = time.perf_counter() - t
+    barrier(world, dev)
+    dt = reduce_max(dt, world, dev)
+    lat = []
+    for k in range(min(200, steps)):
+        t0 = time.perf_counter()
+        tk = g.pipe_submit(rgb_h[k % n_host], dep_h[k % n_host], masks[k % ring])
+        g.pipe_wait(tk, 60000)
+        lat.append((time.perf_counter() - t0) * 1e3)
+    lat.sort()
+    g.close()
+    return {"value": world * steps * H * W / dt / 1e6, "h2d": H * W * 5,
+            "d2h": H * G.mask_words_per_row(W) * 4, "lat_p50": pct(lat, 50), "lat_p99": pct(lat, 99)}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gmm", "reference"], default="gmm")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c1")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="0: same as --steps")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="resident frames to cycle through (0: the workload's sequence length)")
+    ap.add_argument("--cpu-frames", type=int, default=21, help="oracle baseline frames (0 = skip)")
+    ap.add_argument("--cpu-rows", type=int, default=0, help="oracle baseline rows per frame (0 = all)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_gmm(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

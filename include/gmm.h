@@ -1,0 +1,271 @@
+/*
+ * gmm.h - C ABI of the GB300 library for per-pixel Gaussian-mixture
+ * background subtraction of RGB-D frames with counter-based fusion
+ * ("GPU based GMM segmentation of Kinect data", Amamra, Mouats, Aouf).
+ *
+ * Method (§III): every pixel keeps two independent mixtures of M Gaussians
+ * (3 <= M <= 5, §III.A), one on the colour image (3-channel mean, isotropic
+ * variance) and one on the depth map (§III.B, "separated" modalities). Each
+ * new frame is matched against the components in rank order, the matched
+ * component is updated (or the weakest one replaced on a miss), the
+ * components are re-ranked by w / sigma, and a pixel is foreground for a
+ * stream when it does not fit that stream's background set (the best ranked
+ * components whose weights sum above T). The two binary foregrounds are then
+ * fused per pixel with List 1 (§III.C), using a fused label and a counter in
+ * [-3, 3] kept per pixel.
+ *
+ * Model readings where the paper is silent (it defers the update equations
+ * to Stauffer and Grimson): learning rate rho = alpha; colour variance is one
+ * scalar tracking the squared distance summed over channels; rank key
+ * w / sqrt(v), stable; a miss replaces the last-ranked component with
+ * {mu = x, v = init_var, w = init_w}; weights are renormalised every tick;
+ * B = shortest rank prefix with summed weight > T; variances are floored at
+ * v_min; the first frame initialises every component on the sample with
+ * w = 1/M and yields foreground 0; a zero depth reading is invalid (depth
+ * model untouched, depth foreground := colour foreground) and the depth model
+ * of a pixel starts at its first valid reading; List 1 is applied literally,
+ * label and counter starting at 0. The registration of depth into the colour
+ * frame (§III.C) is the identity: inputs are given on one pixel grid.
+ *
+ * Conventions
+ *  - Every int return is a status (GMM_OK or a negative GMM_E* code).
+ *    gmm_last_error() gives a thread-local message for the last failure.
+ *  - Pointers documented as "device" must be device-accessible (device
+ *    allocations, managed or mapped pinned memory); plain pageable host
+ *    pointers are rejected with GMM_EINVAL instead of being dereferenced.
+ *  - The library owns all model state (allocated at create, freed at
+ *    destroy). The caller owns frames and masks and must keep them valid
+ *    until the handle's stream has passed the call's work.
+ *  - Frame layout: rgb8 is H*W*3 bytes, interleaved R,G,B, row-major, row
+ *    stride W*3. depth16 is H*W uint16 millimetres, row stride W, 0 = no
+ *    reading, 2-byte aligned.
+ *  - Mask layout (bit-packed): H rows of gmm_mask_words_per_row(W) =
+ *    ceil(W/32) uint32 words, 4-byte aligned; bit i of word c of row y is
+ *    pixel x = 32*c + i (least significant bit first); bits for x >= W are 0.
+ *  - A CUDA failure is sticky on the handle: later calls return GMM_ECUDA.
+ */
+#ifndef GMM_H
+#define GMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define GMM_OK 0
+#define GMM_EINVAL (-1)   /* bad argument; nothing was launched */
+#define GMM_ENOMEM (-2)   /* device or host allocation failed */
+#define GMM_ECUDA (-3)    /* a CUDA call failed (sticky on the handle) */
+#define GMM_EBUDGET (-4)  /* admission would exceed the pool's state budget */
+#define GMM_ETIMEOUT (-5) /* a bounded wait ran out */
+
+/* ------------------------------------------------------------ state planes */
+/* Per component i (rank order, 0 = best ranked) the state has 8 planes:
+ * colour weight, mean R, G, B, variance; depth weight, mean, variance.
+ * GMM_PLANE_FUSION is the per-pixel List-1 byte: bit 0 fused label, bits
+ * 1-3 counter + 3, bit 4 depth model started. */
+#define GMM_PLANE_W_C 0
+#define GMM_PLANE_MU_R 1
+#define GMM_PLANE_MU_G 2
+#define GMM_PLANE_MU_B 3
+#define GMM_PLANE_V_C 4
+#define GMM_PLANE_W_D 5
+#define GMM_PLANE_MU_D 6
+#define GMM_PLANE_V_D 7
+#define GMM_PLANE_FUSION 8
+#define GMM_NUM_PLANES 8
+
+/* State storage precision. Arithmetic is FP32 in both. */
+#define GMM_PREC_F32 0 /* every plane float32 */
+#define GMM_PREC_F16 1 /* means and variances float16, weights bfloat16 */
+
+typedef struct gmm_ctx gmm_t;
+
+/* Model configuration. gmm_config_init fills the defaults below; edit the
+ * fields, then call gmm_create_ex. */
+typedef struct gmm_config {
+    int H, W;          /* frame size in pixels, >= 1 */
+    int M;             /* components per pixel and stream, 3..5 (§III.A) */
+    float alpha;       /* learning rate, 0 < alpha < 1 */
+    float match_k;     /* match within k standard deviations, > 0 */
+    float bg_T;        /* background weight fraction T, 0 < T < 1 */
+    float init_var;    /* variance of a new colour component (levels^2), > 0 */
+    float init_w;      /* weight of a replacing component, 0 < init_w < 1 */
+    float init_var_d;  /* variance of a new depth component (mm^2), > 0; default init_var */
+    float v_min_c;     /* colour variance floor, > 0; default 1 */
+    float v_min_d;     /* depth variance floor, > 0; default 1 */
+    int precision;     /* GMM_PREC_F32 (default) or GMM_PREC_F16 */
+    int morph_open;    /* 1: mask_out gets a 3x3 opening of the fused mask */
+} gmm_config;
+
+/* Fill *cfg with the given model parameters and the defaults above. */
+void gmm_config_init(gmm_config *cfg, int H, int W, int M, float alpha,
+                     float match_k, float bg_T, float init_var, float init_w);
+
+/* Create a model for H x W frames (§III.A: M Gaussians per pixel, weights
+ * positive and summing to one; §III.B: one mixture per modality). FP32
+ * state, defaults of gmm_config_init. Allocates the state in device memory
+ * of the current CUDA device. Returns NULL on error (GMM_EINVAL for
+ * out-of-range parameters, GMM_ENOMEM, GMM_ECUDA); see gmm_last_error(). */
+gmm_t *gmm_create(int H, int W, int M, float alpha, float match_k, float bg_T,
+                  float init_var, float init_w);
+
+/* As gmm_create, from a full configuration. */
+gmm_t *gmm_create_ex(const gmm_config *cfg);
+
+/* Stream for all later work of the handle (a cudaStream_t; NULL = legacy
+ * default stream). The caller keeps the stream alive. */
+int gmm_set_stream(gmm_t *h, void *cuda_stream);
+
+/* One tick (§III.A-C, §IV): both mixtures and the List-1 fusion for one
+ * RGB-D frame, in one fused kernel. rgb8, depth16: device, read-only.
+ * mask_out: device, receives the fused foreground (bit-packed, see top), or
+ * its 3x3 opening when the handle was created with morph_open = 1.
+ * Asynchronous on the handle's stream. The first call after create (or
+ * gmm_reset) initialises the models from this frame. */
+int gmm_apply(gmm_t *h, const uint8_t *rgb8, const uint16_t *depth16,
+              uint32_t *mask_out);
+
+/* As gmm_apply, and also writes the per-stream foregrounds (colour and
+ * depth, before fusion; bit-packed like mask_out) where the pointers are
+ * not NULL (§V.A compares the colour, depth and fused answers). */
+int gmm_apply_ex(gmm_t *h, const uint8_t *rgb8, const uint16_t *depth16,
+                 uint32_t *mask_out, uint32_t *fg_rgb_out, uint32_t *fg_d_out);
+
+/* One tick from host memory (§IV, Fig. 4(a): frames cross the bus each
+ * tick). rgb8_host, depth16_host: host, read; mask_host: host, written.
+ * Copies the frame in, runs gmm_apply, copies the mask out, and returns when
+ * the mask is in host memory. Staging buffers are owned by the handle and
+ * allocated on first use. Page-locked host buffers give overlapped copies. */
+int gmm_apply_host(gmm_t *h, const uint8_t *rgb8_host,
+                   const uint16_t *depth16_host, uint32_t *mask_host);
+
+/* Pipelined host path (§IV, Fig. 4(a)): queue frame i's upload, compute and
+ * mask download and return at once; up to GMM_PIPE_DEPTH frames may be in
+ * flight, so the upload of frame i+1 and the download of frame i-1 overlap
+ * the compute of frame i. The host buffers must stay valid (and the mask
+ * unread) until gmm_pipe_wait returns for that frame; page-locked buffers
+ * are required for overlap. Returns a ticket >= 0, or a negative status. */
+#define GMM_PIPE_DEPTH 3
+long long gmm_pipe_submit(gmm_t *h, const uint8_t *rgb8_host,
+                          const uint16_t *depth16_host, uint32_t *mask_host);
+
+/* Wait (bounded by timeout_ms; < 0 = no bound) until ticket's mask is in
+ * host memory. GMM_ETIMEOUT if the bound ran out. */
+int gmm_pipe_wait(gmm_t *h, long long ticket, int timeout_ms);
+
+/* Copy one state plane to host memory, converted to float, row-major H*W
+ * (dst_host: host, n >= H*W). plane: GMM_PLANE_*; component: rank 0..M-1
+ * (ignored for GMM_PLANE_FUSION, whose bytes are returned as exact floats).
+ * Synchronous: waits for the handle's stream. */
+int gmm_state_get(const gmm_t *h, int plane, int component, float *dst_host,
+                  size_t n);
+
+/* Load one state plane from host floats (converted to the storage
+ * precision; GMM_PLANE_FUSION takes byte values 0..255). Marks the model as
+ * initialised, so the next tick updates instead of restarting. For tests,
+ * checkpoint restore and migration. Synchronous. */
+int gmm_state_set(gmm_t *h, int plane, int component, const float *src_host,
+                  size_t n);
+
+/* The next tick re-initialises every model from its frame. */
+int gmm_reset(gmm_t *h);
+
+/* Wait for the handle's stream. */
+int gmm_sync(gmm_t *h);
+
+/* Free the state and staging buffers. Waits for outstanding work. */
+int gmm_destroy(gmm_t *h);
+
+/* Thread-local message of the last failed call on this thread. */
+const char *gmm_last_error(void);
+
+/* Words per mask row (ceil(W/32)) and device bytes of one model's state. */
+int gmm_mask_words_per_row(int W);
+size_t gmm_state_bytes(int H, int W, int M, int precision);
+
+/* ---------------------------------------------------- standalone operators */
+/* List 1 (§III.C) alone: fuse two bit-packed binary foregrounds (device,
+ * mask layout) with the per-pixel fusion bytes (device, H*W, updated in
+ * place; only bits 0-3 are used and changed) into mask_out (device).
+ * Asynchronous on `stream`. */
+int gmm_fuse_masks(const uint32_t *fg_rgb, const uint32_t *fg_d,
+                   uint8_t *fusion, uint32_t *mask_out, int H, int W,
+                   void *stream);
+
+/* 3x3 morphological opening (erosion then dilation, 3x3 square, pixels
+ * outside the image are 0) of a bit-packed mask. Not in the paper: an
+ * optional clean-up of the fused output. mask_in, mask_out: device, must not
+ * overlap. Asynchronous on `stream`. */
+int gmm_morph_open3(const uint32_t *mask_in, uint32_t *mask_out, int H, int W,
+                    void *stream);
+
+/* ------------------------------------------------------ multi-camera pool */
+/* Many cameras (the paper's future work, §VI: several RGB-D sensors), each
+ * with its own resident model, advanced together: one persistent kernel
+ * launch per tick walks a tile worklist over every camera that has a frame
+ * submitted. All cameras of a pool share its storage precision. */
+typedef struct gmm_pool gmm_pool_t;
+
+/* budget_bytes: cap on the summed state of admitted cameras (0 = no cap).
+ * max_cams: slot count (>= 1). Allocation of a camera's state happens at
+ * admission. */
+gmm_pool_t *gmm_pool_create(size_t budget_bytes, int precision, int max_cams);
+
+/* Admit a camera (cfg->precision must equal the pool's). Returns its slot
+ * id >= 0, GMM_EBUDGET if its state would exceed the budget, GMM_EINVAL,
+ * GMM_ENOMEM (also when every slot is taken). */
+int gmm_pool_admit(gmm_pool_t *p, const gmm_config *cfg);
+
+/* Free a camera's slot and state. Waits for the pool's stream first. */
+int gmm_pool_release(gmm_pool_t *p, int cam);
+
+/* Queue camera cam's next frame for the next gmm_pool_tick (device
+ * pointers, layouts as gmm_apply; fg pointers may be NULL). A second submit
+ * for the same camera before the tick replaces the first. */
+int gmm_pool_submit(gmm_pool_t *p, int cam, const uint8_t *rgb8,
+                    const uint16_t *depth16, uint32_t *mask_out,
+                    uint32_t *fg_rgb_out, uint32_t *fg_d_out);
+
+/* Advance every submitted camera by one frame in one launch (asynchronous
+ * on the pool's stream), then clear the submissions. */
+int gmm_pool_tick(gmm_pool_t *p);
+
+int gmm_pool_set_stream(gmm_pool_t *p, void *cuda_stream);
+
+/* Launch shape of the persistent kernel: threads per block (64..512, a
+ * multiple of 32), CTAs per SM (>= 1), pixels per tile (a multiple of the
+ * block size). 0 keeps the current value. */
+int gmm_pool_set_launch(gmm_pool_t *p, int threads, int ctas_per_sm,
+                        int tile_pixels);
+
+/* Time each candidate launch shape on the current submissions (the state is
+ * snapshotted and restored around the trials, so the models do not move)
+ * and keep the fastest. Requires a submitted tick; leaves it submitted.
+ * Writes the chosen shape to *threads, *ctas_per_sm, *tile_pixels when not
+ * NULL. Synchronous. */
+int gmm_pool_autotune(gmm_pool_t *p, int iters, int *threads,
+                      int *ctas_per_sm, int *tile_pixels);
+
+/* Capture the pool's tick in a CUDA graph (enable = 1) and replay it while
+ * the set of submitted cameras and their buffers is unchanged. */
+int gmm_pool_use_graph(gmm_pool_t *p, int enable);
+
+/* As gmm_state_get, for camera cam. */
+int gmm_pool_state_get(const gmm_pool_t *p, int cam, int plane, int component,
+                       float *dst_host, size_t n);
+
+/* Summed state bytes of admitted cameras, and the budget. */
+size_t gmm_pool_state_used(const gmm_pool_t *p);
+
+int gmm_pool_sync(gmm_pool_t *p);
+int gmm_pool_destroy(gmm_pool_t *p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMM_H */

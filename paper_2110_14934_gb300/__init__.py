@@ -1,0 +1,372 @@
+"""GB300 (sm_103a) per-pixel RGB-D Gaussian-mixture background subtraction
+with counter-based fusion ("GPU based GMM segmentation of Kinect data").
+
+This module is a thin binding of the C ABI in ``include/gmm.h``: it marshals
+torch tensors (device memory, streams) and numpy arrays into plain pointers
+and sizes. Every step of the method runs in the CUDA kernels of
+``libgmm.so``; there is no CPU fallback, and using the package without the
+built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["GMM", "Pool", "GMMError", "fuse_masks", "morph_open3", "mask_words_per_row",
+           "state_bytes", "unpack_mask", "pack_mask", "load_library", "PLANES",
+           "PREC_F32", "PREC_F16"]
+
+OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT = 0, -1, -2, -3, -4, -5
+PLANE_W_C, PLANE_MU_R, PLANE_MU_G, PLANE_MU_B, PLANE_V_C, PLANE_W_D, PLANE_MU_D, PLANE_V_D, \
+    PLANE_FUSION = range(9)
+PLANES = ("w_c", "mu_r", "mu_g", "mu_b", "v_c", "w_d", "mu_d", "v_d")
+PREC_F32, PREC_F16 = 0, 1
+PIPE_DEPTH = 3
+
+_ERRNAMES = {EINVAL: "GMM_EINVAL", ENOMEM: "GMM_ENOMEM", ECUDA: "GMM_ECUDA",
+             EBUDGET: "GMM_EBUDGET", ETIMEOUT: "GMM_ETIMEOUT"}
+
+
+class GMMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GMMConfig(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("M", ctypes.c_int),
+                ("alpha", ctypes.c_float), ("match_k", ctypes.c_float), ("bg_T", ctypes.c_float),
+                ("init_var", ctypes.c_float), ("init_w", ctypes.c_float),
+                ("init_var_d", ctypes.c_float), ("v_min_c", ctypes.c_float),
+                ("v_min_d", ctypes.c_float), ("precision", ctypes.c_int),
+                ("morph_open", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Load libgmm.so (building it first when stale). Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed and _build.stale():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libgmm.so is not built ({_build.LIB}); run __graft_entry__.build()")
+    L = ctypes.CDLL(_build.LIB)
+    sig = {
+        "gmm_config_init": (None, [ctypes.POINTER(GMMConfig), ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int] + [ctypes.c_float] * 5),
+        "gmm_create": (_vp, [ctypes.c_int] * 3 + [ctypes.c_float] * 5),
+        "gmm_create_ex": (_vp, [ctypes.POINTER(GMMConfig)]),
+        "gmm_set_stream": (ctypes.c_int, [_vp, _vp]),
+        "gmm_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "gmm_apply_ex": (ctypes.c_int, [_vp] * 6),
+        "gmm_apply_host": (ctypes.c_int, [_vp] * 4),
+        "gmm_pipe_submit": (ctypes.c_longlong, [_vp] * 4),
+        "gmm_pipe_wait": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_int]),
+        "gmm_state_get": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t]),
+        "gmm_state_set": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t]),
+        "gmm_reset": (ctypes.c_int, [_vp]),
+        "gmm_sync": (ctypes.c_int, [_vp]),
+        "gmm_destroy": (ctypes.c_int, [_vp]),
+        "gmm_last_error": (ctypes.c_char_p, []),
+        "gmm_mask_words_per_row": (ctypes.c_int, [ctypes.c_int]),
+        "gmm_state_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
+        "gmm_fuse_masks": (ctypes.c_int, [_vp] * 4 + [ctypes.c_int, ctypes.c_int, _vp]),
+        "gmm_morph_open3": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp]),
+        "gmm_pool_create": (_vp, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
+        "gmm_pool_admit": (ctypes.c_int, [_vp, ctypes.POINTER(GMMConfig)]),
+        "gmm_pool_release": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "gmm_pool_submit": (ctypes.c_int, [_vp, ctypes.c_int] + [_vp] * 5),
+        "gmm_pool_tick": (ctypes.c_int, [_vp]),
+        "gmm_pool_set_stream": (ctypes.c_int, [_vp, _vp]),
+        "gmm_pool_set_launch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "gmm_pool_autotune": (ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3),
+        "gmm_pool_use_graph": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "gmm_pool_state_get": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
+                                              ctypes.c_size_t]),
+        "gmm_pool_state_used": (ctypes.c_size_t, [_vp]),
+        "gmm_pool_sync": (ctypes.c_int, [_vp]),
+        "gmm_pool_destroy": (ctypes.c_int, [_vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _err() -> str:
+    return (load_library().gmm_last_error() or b"").decode(errors="replace")
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise GMMError(rc, _err())
+    return rc
+
+
+def mask_words_per_row(W: int) -> int:
+    return (int(W) + 31) // 32
+
+
+def state_bytes(H: int, W: int, M: int, precision: int = PREC_F32) -> int:
+    return int(load_library().gmm_state_bytes(H, W, M, precision))
+
+
+def unpack_mask(words, H: int, W: int) -> np.ndarray:
+    """Bit-packed mask (H rows of ceil(W/32) uint32, LSB first) -> bool [H, W]."""
+    a = np.asarray(words).astype(np.uint32, copy=False).reshape(H, mask_words_per_row(W))
+    bits = np.unpackbits(a.view(np.uint8).reshape(H, -1), axis=1, bitorder="little")
+    return bits[:, :W].astype(bool)
+
+
+def pack_mask(mask: np.ndarray) -> np.ndarray:
+    """bool [H, W] -> uint32 [H, ceil(W/32)] in the library's mask layout."""
+    m = np.asarray(mask).astype(bool)
+    H, W = m.shape
+    wpr = mask_words_per_row(W)
+    padded = np.zeros((H, wpr * 32), dtype=np.uint8)
+    padded[:, :W] = m
+    return np.packbits(padded, axis=1, bitorder="little").view(np.uint32).reshape(H, wpr)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if not t.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return t.ctypes.data
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream, device) -> int:
+    import torch
+    s = torch.cuda.current_stream(device) if stream is None else stream
+    return s.cuda_stream
+
+
+def _check_frame(rgb, depth, H, W):
+    if tuple(rgb.shape[-3:]) != (H, W, 3) or rgb.element_size() != 1:
+        raise ValueError(f"rgb must be uint8 [{H}, {W}, 3]")
+    if tuple(depth.shape[-2:]) != (H, W) or depth.element_size() != 2:
+        raise ValueError(f"depth must be a 16-bit [{H}, {W}] tensor")
+
+
+class GMM:
+    """One camera's resident model (FP32 or FP16/BF16 state) on a CUDA device."""
+
+    def __init__(self, H, W, M=3, alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0,
+                 init_w=0.05, init_var_d=None, v_min_c=1.0, v_min_d=1.0,
+                 precision=PREC_F32, morph_open=False, device=None):
+        import torch
+        L = load_library()
+        self.device = torch.device("cuda" if device is None else device)
+        cfg = GMMConfig()
+        L.gmm_config_init(ctypes.byref(cfg), H, W, M, alpha, match_k, bg_T, init_var, init_w)
+        if init_var_d is not None:
+            cfg.init_var_d = init_var_d
+        cfg.v_min_c = v_min_c
+        cfg.v_min_d = v_min_d
+        cfg.precision = precision
+        cfg.morph_open = int(bool(morph_open))
+        self.cfg = cfg
+        self.H, self.W, self.M = int(H), int(W), int(M)
+        self.wpr = mask_words_per_row(W)
+        with torch.cuda.device(self.device):
+            h = L.gmm_create_ex(ctypes.byref(cfg))
+        if not h:
+            raise GMMError(EINVAL, _err())
+        self._h = h
+
+    # -- ticks -----------------------------------------------------------------
+    def new_mask(self):
+        import torch
+        return torch.empty((self.H, self.wpr), dtype=torch.int32, device=self.device)
+
+    def apply(self, rgb, depth, mask=None, fg_rgb=None, fg_d=None, stream=None):
+        """One tick on device tensors; returns the mask tensor (int32 words)."""
+        _check_frame(rgb, depth, self.H, self.W)
+        mask = self.new_mask() if mask is None else mask
+        L = load_library()
+        _check(L.gmm_set_stream(self._h, _stream_ptr(stream, self.device)))
+        _check(L.gmm_apply_ex(self._h, _ptr(rgb), _ptr(depth), _ptr(mask), _ptr(fg_rgb),
+                              _ptr(fg_d)))
+        return mask
+
+    def apply_host(self, rgb: np.ndarray, depth: np.ndarray, mask: np.ndarray | None = None):
+        """One tick from host memory (copies inside); returns the host mask words."""
+        rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+        depth = np.ascontiguousarray(depth).view(np.uint16)
+        if mask is None:
+            mask = np.empty((self.H, self.wpr), dtype=np.uint32)
+        _check(load_library().gmm_apply_host(self._h, _ptr(rgb), _ptr(depth), _ptr(mask)))
+        return mask
+
+    def pipe_submit(self, rgb, depth, mask) -> int:
+        """Queue a host-memory tick (buffers: pinned torch CPU tensors or numpy)."""
+        return _check(load_library().gmm_pipe_submit(self._h, _ptr(rgb), _ptr(depth), _ptr(mask)))
+
+    def pipe_wait(self, ticket: int, timeout_ms: int = -1) -> None:
+        _check(load_library().gmm_pipe_wait(self._h, ticket, timeout_ms))
+
+    def set_stream(self, stream) -> None:
+        _check(load_library().gmm_set_stream(self._h, _stream_ptr(stream, self.device)))
+
+    # -- state -----------------------------------------------------------------
+    def state_get(self, plane: int, component: int = 0) -> np.ndarray:
+        out = np.empty((self.H, self.W), dtype=np.float32)
+        _check(load_library().gmm_state_get(self._h, plane, component, _ptr(out), out.size))
+        return out
+
+    def state_set(self, plane: int, component: int, values: np.ndarray) -> None:
+        v = np.ascontiguousarray(values, dtype=np.float32).reshape(self.H, self.W)
+        _check(load_library().gmm_state_set(self._h, plane, component, _ptr(v), v.size))
+
+    def planes(self) -> np.ndarray:
+        """Whole state as float32 [M, 8, H, W] (planes in PLANES order)."""
+        return np.stack([np.stack([self.state_get(f, i) for f in range(8)]) for i in range(self.M)])
+
+    def fusion(self) -> np.ndarray:
+        return self.state_get(PLANE_FUSION).astype(np.uint8)
+
+    def load_state(self, planes: np.ndarray, fusion: np.ndarray) -> None:
+        planes = np.asarray(planes, dtype=np.float32).reshape(self.M, 8, self.H, self.W)
+        for i in range(self.M):
+            for f in range(8):
+                self.state_set(f, i, planes[i, f])
+        self.state_set(PLANE_FUSION, 0, np.asarray(fusion, dtype=np.float32))
+
+    def reset(self) -> None:
+        _check(load_library().gmm_reset(self._h))
+
+    def sync(self) -> None:
+        _check(load_library().gmm_sync(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load_library().gmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pool:
+    """Many cameras with resident models advanced together, one persistent
+    launch per tick."""
+
+    def __init__(self, budget_bytes=0, precision=PREC_F32, max_cams=256, device=None):
+        import torch
+        L = load_library()
+        self.device = torch.device("cuda" if device is None else device)
+        self.precision = precision
+        with torch.cuda.device(self.device):
+            p = L.gmm_pool_create(budget_bytes, precision, max_cams)
+        if not p:
+            raise GMMError(EINVAL, _err())
+        self._p = p
+        self.cams = {}
+
+    def admit(self, H, W, M=3, alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0, init_w=0.05,
+              init_var_d=None, v_min_c=1.0, v_min_d=1.0) -> int:
+        """Returns the camera id; raises GMMError (code EBUDGET) when the state
+        budget is exhausted."""
+        L = load_library()
+        cfg = GMMConfig()
+        L.gmm_config_init(ctypes.byref(cfg), H, W, M, alpha, match_k, bg_T, init_var, init_w)
+        if init_var_d is not None:
+            cfg.init_var_d = init_var_d
+        cfg.v_min_c = v_min_c
+        cfg.v_min_d = v_min_d
+        cfg.precision = self.precision
+        cam = _check(L.gmm_pool_admit(self._p, ctypes.byref(cfg)))
+        self.cams[cam] = (int(H), int(W), int(M))
+        return cam
+
+    def release(self, cam: int) -> None:
+        _check(load_library().gmm_pool_release(self._p, cam))
+        self.cams.pop(cam, None)
+
+    def submit(self, cam, rgb, depth, mask, fg_rgb=None, fg_d=None) -> None:
+        H, W, _ = self.cams[cam]
+        _check_frame(rgb, depth, H, W)
+        _check(load_library().gmm_pool_submit(self._p, cam, _ptr(rgb), _ptr(depth), _ptr(mask),
+                                              _ptr(fg_rgb), _ptr(fg_d)))
+
+    def tick(self, stream=None) -> None:
+        L = load_library()
+        _check(L.gmm_pool_set_stream(self._p, _stream_ptr(stream, self.device)))
+        _check(L.gmm_pool_tick(self._p))
+
+    def set_stream(self, stream) -> None:
+        _check(load_library().gmm_pool_set_stream(self._p, _stream_ptr(stream, self.device)))
+
+    def set_launch(self, threads=0, ctas_per_sm=0, tile_pixels=0) -> None:
+        _check(load_library().gmm_pool_set_launch(self._p, threads, ctas_per_sm, tile_pixels))
+
+    def autotune(self, iters=3):
+        t, c, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load_library().gmm_pool_autotune(self._p, iters, ctypes.byref(t), ctypes.byref(c),
+                                                ctypes.byref(p)))
+        return {"threads": t.value, "ctas_per_sm": c.value, "tile_pixels": p.value}
+
+    def use_graph(self, enable=True) -> None:
+        _check(load_library().gmm_pool_use_graph(self._p, int(bool(enable))))
+
+    def state_get(self, cam, plane, component=0) -> np.ndarray:
+        H, W, _ = self.cams[cam]
+        out = np.empty((H, W), dtype=np.float32)
+        _check(load_library().gmm_pool_state_get(self._p, cam, plane, component, _ptr(out),
+                                                 out.size))
+        return out
+
+    def planes(self, cam) -> np.ndarray:
+        H, W, M = self.cams[cam]
+        return np.stack([np.stack([self.state_get(cam, f, i) for f in range(8)]) for i in range(M)])
+
+    def fusion(self, cam) -> np.ndarray:
+        return self.state_get(cam, PLANE_FUSION).astype(np.uint8)
+
+    def state_used(self) -> int:
+        return int(load_library().gmm_pool_state_used(self._p))
+
+    def sync(self) -> None:
+        _check(load_library().gmm_pool_sync(self._p))
+
+    def close(self) -> None:
+        if getattr(self, "_p", None):
+            load_library().gmm_pool_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fuse_masks(fg_rgb, fg_d, fusion, mask_out, H, W, stream=None) -> None:
+    """List 1 alone on bit-packed device masks; fusion bytes updated in place."""
+    _check(load_library().gmm_fuse_masks(_ptr(fg_rgb), _ptr(fg_d), _ptr(fusion), _ptr(mask_out),
+                                         H, W, _stream_ptr(stream, fusion.device)))
+
+
+def morph_open3(mask_in, mask_out, H, W, stream=None) -> None:
+    """3x3 opening of a bit-packed device mask."""
+    _check(load_library().gmm_morph_open3(_ptr(mask_in), _ptr(mask_out), H, W,
+                                          _stream_ptr(stream, mask_in.device)))

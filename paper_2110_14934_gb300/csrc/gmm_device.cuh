@@ -1,0 +1,315 @@
+// Per-pixel device code shared by the single-camera tick kernel and the
+// multi-camera persistent kernel: state loads/stores for both storage
+// precisions, one mixture step (match, update or replace, re-rank,
+// background test), List-1 fusion, and the bit-packed mask write.
+//
+// State layout in device memory (one camera): M*8 planes, component-major,
+// plane index = 8*i + field with fields {w_c, mu_r, mu_g, mu_b, v_c, w_d,
+// mu_d, v_d}; each plane holds H*w_pad elements (rows padded to a multiple of
+// 32 pixels, so 32 consecutive pixels of a warp map to one mask word) and
+// starts at a multiple of `stride` elements. A warp reads 32 consecutive
+// elements of each plane: one fully used 128-byte line per plane in FP32.
+// The List-1 byte of a pixel lives in a separate H*w_pad byte array.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace gmmdev {
+
+constexpr int kFields = 8;
+enum { F_WC = 0, F_MUR, F_MUG, F_MUB, F_VC, F_WD, F_MUD, F_VD };
+constexpr uint32_t kDepthStarted = 16u;
+
+struct StreamPrm {
+    float alpha, oma, k2, T, init_var, init_w, v_min, pad;
+};
+
+// Everything one tick of one camera needs; passed by value to the
+// single-camera kernel, read from a device table by the pooled kernel.
+struct CamView {
+    void *planes;          // M*8 planes of `stride` elements
+    uint8_t *fusion;       // H*w_pad List-1 bytes
+    const uint8_t *rgb;    // H*W*3, interleaved
+    const uint16_t *depth; // H*W, millimetres, 0 = invalid
+    uint32_t *mask;        // H*wpr words: fused foreground
+    uint32_t *fg_rgb;      // optional colour foreground words (may be null)
+    uint32_t *fg_d;        // optional depth foreground words (may be null)
+    int64_t stride;        // plane stride in elements
+    int64_t n_pad;         // H*w_pad
+    int H, W, w_pad, wpr;  // wpr = words per mask row = w_pad / 32
+    int M, prec, first, pad;
+    StreamPrm pc, pd;
+};
+
+// ------------------------------------------------------------ storage types
+template <int PREC> struct Storage;
+template <> struct Storage<0> {
+    static constexpr int kBytes = 4;
+    static __device__ __forceinline__ float ldw(const void *b, int64_t o) {
+        return static_cast<const float *>(b)[o];
+    }
+    static __device__ __forceinline__ float ldv(const void *b, int64_t o) {
+        return static_cast<const float *>(b)[o];
+    }
+    static __device__ __forceinline__ void stw(void *b, int64_t o, float v) {
+        static_cast<float *>(b)[o] = v;
+    }
+    static __device__ __forceinline__ void stv(void *b, int64_t o, float v) {
+        static_cast<float *>(b)[o] = v;
+    }
+};
+// Means and variances in float16, weights in bfloat16 (weights need range
+// near zero more than mantissa). Values above the float16 range are clamped
+// to its largest finite value instead of becoming infinite.
+template <> struct Storage<1> {
+    static constexpr int kBytes = 2;
+    static __device__ __forceinline__ float ldw(const void *b, int64_t o) {
+        return __bfloat162float(static_cast<const __nv_bfloat16 *>(b)[o]);
+    }
+    static __device__ __forceinline__ float ldv(const void *b, int64_t o) {
+        return __half2float(static_cast<const __half *>(b)[o]);
+    }
+    static __device__ __forceinline__ void stw(void *b, int64_t o, float v) {
+        static_cast<__nv_bfloat16 *>(b)[o] = __float2bfloat16_rn(v);
+    }
+    static __device__ __forceinline__ void stv(void *b, int64_t o, float v) {
+        static_cast<__half *>(b)[o] = __float2half_rn(fminf(v, 65504.0f));
+    }
+};
+
+// ------------------------------------------------------------ mixture step
+template <int D> struct Comp {
+    float key;
+    int idx;
+    float w, v;
+    float mu[D];
+};
+
+template <int D>
+__device__ __forceinline__ void comp_swap_if(Comp<D> &a, Comp<D> &b) {
+    // a sits before b. Descending key; equal keys keep the lower stored index
+    // first, which makes the order total and the network's result the stable
+    // sort.
+    const bool sw = (b.key > a.key) || (b.key == a.key && b.idx < a.idx);
+    Comp<D> lo = sw ? b : a;
+    Comp<D> hi = sw ? a : b;
+    a = lo;
+    b = hi;
+}
+
+// Optimal compare-exchange networks for 3, 4 and 5 elements.
+template <int M, int D> __device__ __forceinline__ void rank_sort(Comp<D> (&c)[M]);
+template <> __device__ __forceinline__ void rank_sort<3, 3>(Comp<3> (&c)[3]) {
+    comp_swap_if(c[0], c[1]); comp_swap_if(c[0], c[2]); comp_swap_if(c[1], c[2]);
+}
+template <> __device__ __forceinline__ void rank_sort<3, 1>(Comp<1> (&c)[3]) {
+    comp_swap_if(c[0], c[1]); comp_swap_if(c[0], c[2]); comp_swap_if(c[1], c[2]);
+}
+template <int D> __device__ __forceinline__ void net4(Comp<D> (&c)[4]) {
+    comp_swap_if(c[0], c[1]); comp_swap_if(c[2], c[3]); comp_swap_if(c[0], c[2]);
+    comp_swap_if(c[1], c[3]); comp_swap_if(c[1], c[2]);
+}
+template <> __device__ __forceinline__ void rank_sort<4, 3>(Comp<3> (&c)[4]) { net4(c); }
+template <> __device__ __forceinline__ void rank_sort<4, 1>(Comp<1> (&c)[4]) { net4(c); }
+template <int D> __device__ __forceinline__ void net5(Comp<D> (&c)[5]) {
+    comp_swap_if(c[0], c[1]); comp_swap_if(c[3], c[4]); comp_swap_if(c[2], c[4]);
+    comp_swap_if(c[2], c[3]); comp_swap_if(c[0], c[3]); comp_swap_if(c[0], c[2]);
+    comp_swap_if(c[1], c[4]); comp_swap_if(c[1], c[3]); comp_swap_if(c[1], c[2]);
+}
+template <> __device__ __forceinline__ void rank_sort<5, 3>(Comp<3> (&c)[5]) { net5(c); }
+template <> __device__ __forceinline__ void rank_sort<5, 1>(Comp<1> (&c)[5]) { net5(c); }
+
+// One tick of one mixture at one pixel (§III.A). The components are in rank
+// order on entry and on exit. Returns the stream's foreground bit.
+template <int M, int D>
+__device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D],
+                                            const StreamPrm &p) {
+    // Match: first component, in rank order, within k standard deviations.
+    int j = -1;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        float d2 = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < D; ++ch) {
+            const float df = x[ch] - c[i].mu[ch];
+            d2 = fmaf(df, df, d2);
+        }
+        if (j < 0 && d2 < p.k2 * c[i].v)
+            j = i;
+    }
+    const bool matched = j >= 0;
+    const int jj = matched ? j : M - 1;
+
+    // Weights decay; the matched one gains alpha, or the last-ranked one is
+    // replaced on a miss; then renormalise.
+    float sum = 0.f;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        float w = c[i].w * p.oma;
+        if (i == jj)
+            w = matched ? w + p.alpha : p.init_w;
+        c[i].w = w;
+        sum += w;
+    }
+    const float inv = 1.0f / sum;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        c[i].w *= inv;
+        c[i].idx = i;
+        if (i == jj) {
+            if (matched) {
+                float d2 = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < D; ++ch) {
+                    const float m = fmaf(p.oma, c[i].mu[ch], p.alpha * x[ch]);
+                    c[i].mu[ch] = m;
+                    const float df = x[ch] - m;
+                    d2 = fmaf(df, df, d2);
+                }
+                c[i].v = fmaxf(p.v_min, fmaf(p.oma, c[i].v, p.alpha * d2));
+            } else {
+#pragma unroll
+                for (int ch = 0; ch < D; ++ch)
+                    c[i].mu[ch] = x[ch];
+                c[i].v = p.init_var;
+            }
+        }
+        c[i].key = c[i].w * rsqrtf(c[i].v);
+    }
+
+    // Re-rank by w / sigma (stable), then the background test.
+    rank_sort<M, D>(c);
+    int rank = 0, B = M;
+    float acc = 0.f;
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        if (c[r].idx == jj)
+            rank = r;
+        acc += c[r].w;
+        if (B == M && acc > p.T)
+            B = r + 1;
+    }
+    return (!matched || rank >= B) ? 1 : 0;
+}
+
+// List 1 (§III.C) on the low four bits of the per-pixel byte.
+__device__ __forceinline__ uint32_t fuse_list1(int fgc, int fgd, uint32_t fb) {
+    int F = (int)(fb & 1u);
+    int cpt = (int)((fb >> 1) & 7u) - 3;
+    if (fgc == fgd) {
+        F = fgd;
+        cpt = 0;
+    } else if (cpt == 3) {
+        F = fgc;
+        cpt = 0;
+    } else if (cpt == -3) {
+        F = fgd;
+        cpt = 0;
+    } else if (F == fgc) {
+        cpt += 1;
+    } else {
+        cpt -= 1;
+    }
+    return (fb & ~15u) | (uint32_t)F | ((uint32_t)(cpt + 3) << 1);
+}
+
+// ------------------------------------------------------------ one pixel
+// p: padded linear pixel index (row * w_pad + x). Returns bit 0 fused label,
+// bit 1 colour foreground, bit 2 depth foreground (all 0 for padding).
+template <int M, int PREC>
+__device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) {
+    using S = Storage<PREC>;
+    const int64_t row = (p >> 5) / cv.wpr;
+    const int x = (int)(p - row * cv.w_pad);
+    if (x >= cv.W)
+        return 0u;
+    const int64_t q = row * cv.W + x;
+    const float xc[3] = {(float)cv.rgb[3 * q], (float)cv.rgb[3 * q + 1],
+                         (float)cv.rgb[3 * q + 2]};
+    const uint32_t draw = cv.depth[q];
+    const float xd[1] = {(float)draw};
+    const int64_t st = cv.stride;
+    const void *pl = cv.planes;
+
+    Comp<3> c[M];
+    Comp<1> d[M];
+    uint32_t fb;
+    int fgc, fgd;
+    if (cv.first) {
+        fb = 0u;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            c[i].w = 1.0f / (float)M;
+            c[i].mu[0] = xc[0]; c[i].mu[1] = xc[1]; c[i].mu[2] = xc[2];
+            c[i].v = cv.pc.init_var;
+            d[i].w = 0.f; d[i].mu[0] = 0.f; d[i].v = 0.f;
+        }
+        fgc = 0;
+    } else {
+        fb = cv.fusion[p];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int64_t b = (int64_t)(kFields * i) * st + p;
+            c[i].w = S::ldw(pl, b + F_WC * st);
+            c[i].mu[0] = S::ldv(pl, b + F_MUR * st);
+            c[i].mu[1] = S::ldv(pl, b + F_MUG * st);
+            c[i].mu[2] = S::ldv(pl, b + F_MUB * st);
+            c[i].v = S::ldv(pl, b + F_VC * st);
+            d[i].w = S::ldw(pl, b + F_WD * st);
+            d[i].mu[0] = S::ldv(pl, b + F_MUD * st);
+            d[i].v = S::ldv(pl, b + F_VD * st);
+        }
+        fgc = mixture_step<M, 3>(c, xc, cv.pc);
+    }
+
+    if (draw == 0u) {
+        fgd = fgc; // no reading: depth model untouched, depth answer = colour
+    } else if (!(fb & kDepthStarted)) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            d[i].w = 1.0f / (float)M;
+            d[i].mu[0] = xd[0];
+            d[i].v = cv.pd.init_var;
+        }
+        fb |= kDepthStarted;
+        fgd = 0;
+    } else {
+        fgd = mixture_step<M, 1>(d, xd, cv.pd);
+    }
+    fb = fuse_list1(fgc, fgd, fb);
+
+    void *plw = cv.planes;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const int64_t b = (int64_t)(kFields * i) * st + p;
+        S::stw(plw, b + F_WC * st, c[i].w);
+        S::stv(plw, b + F_MUR * st, c[i].mu[0]);
+        S::stv(plw, b + F_MUG * st, c[i].mu[1]);
+        S::stv(plw, b + F_MUB * st, c[i].mu[2]);
+        S::stv(plw, b + F_VC * st, c[i].v);
+        S::stw(plw, b + F_WD * st, d[i].w);
+        S::stv(plw, b + F_MUD * st, d[i].mu[0]);
+        S::stv(plw, b + F_VD * st, d[i].v);
+    }
+    cv.fusion[p] = (uint8_t)fb;
+    return (fb & 1u) | ((uint32_t)fgc << 1) | ((uint32_t)fgd << 2);
+}
+
+// All 32 lanes of the warp call this for 32 consecutive padded pixels
+// starting at a multiple of 32 (word index wi).
+__device__ __forceinline__ void write_mask_words(const CamView &cv, int64_t wi, uint32_t bits) {
+    const uint32_t F = __ballot_sync(0xffffffffu, bits & 1u);
+    const uint32_t fc = __ballot_sync(0xffffffffu, bits & 2u);
+    const uint32_t fd = __ballot_sync(0xffffffffu, bits & 4u);
+    if ((threadIdx.x & 31u) == 0u) {
+        cv.mask[wi] = F;
+        if (cv.fg_rgb)
+            cv.fg_rgb[wi] = fc;
+        if (cv.fg_d)
+            cv.fg_d[wi] = fd;
+    }
+}
+
+} // namespace gmmdev

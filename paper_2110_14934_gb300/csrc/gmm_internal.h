@@ -1,0 +1,38 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gmm_device.cuh"
+
+namespace gmmhost {
+
+// Single-camera tick: one thread per padded pixel. threads: block size.
+cudaError_t launch_tick(const gmmdev::CamView &cv, int threads, cudaStream_t s);
+
+// List 1 alone over bit-packed inputs.
+cudaError_t launch_fuse(const uint32_t *fg_rgb, const uint32_t *fg_d, uint8_t *fusion,
+                        uint32_t *mask, int H, int W, cudaStream_t s);
+
+// 3x3 opening of a bit-packed mask.
+cudaError_t launch_morph_open3(const uint32_t *in, uint32_t *out, int H, int W,
+                               cudaStream_t s);
+
+// Multi-camera persistent tick. The worklist is implicit: job j covers tiles
+// [tile_begin[j], tile_begin[j+1]) of camera views[j], tile_pixels pixels
+// each (the last one of a camera ragged). counter must be zero at launch.
+struct PoolArgs {
+    const gmmdev::CamView *views;
+    const int64_t *tile_begin; // n_jobs + 1 entries
+    int *counter;
+    int n_jobs;
+    int tile_pixels;
+    int64_t n_tiles;
+};
+cudaError_t launch_pool_tick_impl(const PoolArgs &a, int threads, int blocks, int prec,
+                                  cudaStream_t s);
+
+int num_sms();
+
+} // namespace gmmhost

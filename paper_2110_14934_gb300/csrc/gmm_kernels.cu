@@ -1,0 +1,252 @@
+// Kernels: single-camera tick, multi-camera persistent tick, List 1 alone,
+// and the 3x3 opening of a bit-packed mask.
+//
+// The tick is HBM-bound: per pixel it reads and writes the whole mixture
+// state (64*M bytes in FP32, 32*M in FP16/BF16) plus 5 bytes of frame, the
+// List-1 byte and 1/8 byte of mask. There is no dense contraction, so there
+// is no tensor-core work; the design goal is full-line coalesced traffic
+// with enough bytes in flight per SM.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gmm_internal.h"
+
+using namespace gmmdev;
+using gmmhost::PoolArgs;
+
+namespace {
+
+// ------------------------------------------------------------ single camera
+template <int M, int PREC>
+__global__ void __launch_bounds__(256) k_tick(const CamView cv) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= cv.n_pad) // n_pad is a multiple of 32: whole warps leave
+        return;
+    const uint32_t bits = process_pixel<M, PREC>(cv, p);
+    write_mask_words(cv, p >> 5, bits);
+}
+
+template <int M, int PREC>
+cudaError_t launch_tick_t(const CamView &cv, int threads, cudaStream_t s) {
+    const int64_t blocks = (cv.n_pad + threads - 1) / threads;
+    k_tick<M, PREC><<<(unsigned)blocks, threads, 0, s>>>(cv);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ multi camera
+// CTAs take tiles of the implicit worklist (PoolArgs) from an atomic counter;
+// the camera of a tile is found by binary search over tile_begin, and its
+// CamView is staged in shared memory for the whole tile.
+template <int M, int PREC>
+__device__ __forceinline__ void pool_tile(const CamView &cv, int64_t p0, int64_t p1) {
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        // p1 - p0 is a multiple of 32 and blockDim too: warps stay whole.
+        const uint32_t bits = process_pixel<M, PREC>(cv, p);
+        write_mask_words(cv, p >> 5, bits);
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(512) k_pool_tick(const PoolArgs a) {
+    __shared__ CamView s_cv;
+    __shared__ int64_t s_tile;
+    __shared__ int s_job;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int64_t t = atomicAdd(a.counter, 1);
+            int lo = 0, hi = a.n_jobs - 1;
+            if (t < a.n_tiles) {
+                while (lo < hi) { // last job with tile_begin <= t
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (a.tile_begin[mid] <= t)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+            }
+            s_tile = t;
+            s_job = lo;
+        }
+        __syncthreads();
+        const int64_t t = s_tile;
+        if (t >= a.n_tiles)
+            return;
+        const int job = s_job;
+        {
+            const int *src = reinterpret_cast<const int *>(a.views + job);
+            int *dst = reinterpret_cast<int *>(&s_cv);
+            for (int i = threadIdx.x; i < (int)(sizeof(CamView) / 4); i += blockDim.x)
+                dst[i] = src[i];
+        }
+        __syncthreads();
+        const int64_t p0 = (t - a.tile_begin[job]) * a.tile_pixels;
+        const int64_t p1 = min(p0 + (int64_t)a.tile_pixels, s_cv.n_pad);
+        switch (s_cv.M) {
+        case 3: pool_tile<3, PREC>(s_cv, p0, p1); break;
+        case 4: pool_tile<4, PREC>(s_cv, p0, p1); break;
+        default: pool_tile<5, PREC>(s_cv, p0, p1); break;
+        }
+        __syncthreads(); // s_cv and s_tile are rewritten next round
+    }
+}
+
+// ------------------------------------------------------------ List 1 alone
+__global__ void __launch_bounds__(256) k_fuse(const uint32_t *fg_rgb, const uint32_t *fg_d,
+                                              uint8_t *fusion, uint32_t *mask, int H, int W,
+                                              int wpr) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n_pad = (int64_t)H * wpr * 32;
+    if (p >= n_pad)
+        return;
+    const int64_t wi = p >> 5;
+    const int64_t row = wi / wpr;
+    const int x = (int)(p - row * wpr * 32);
+    const int lane = (int)(p & 31);
+    uint32_t F = 0u;
+    if (x < W) {
+        const int fc = (int)((fg_rgb[wi] >> lane) & 1u);
+        const int fd = (int)((fg_d[wi] >> lane) & 1u);
+        const int64_t q = row * W + x;
+        const uint32_t fb = fuse_list1(fc, fd, fusion[q]);
+        fusion[q] = (uint8_t)fb;
+        F = fb & 1u;
+    }
+    const uint32_t word = __ballot_sync(0xffffffffu, F);
+    if (lane == 0)
+        mask[wi] = word;
+}
+
+// ------------------------------------------------------------ 3x3 opening
+// A CTA of 32 x 8 threads produces an 8-row x 32-word tile. It stages the
+// input tile with a 2-row and 2-word halo in shared memory, erodes (AND of
+// the 3x3 neighbourhood, outside = 0) into a 1-row/1-word halo, then dilates
+// (OR) into the output. Bit i of a word is pixel 32*word + i, so the left
+// neighbour of bit i is bit i-1 (x << 1) and bit 0 takes bit 31 of the word
+// on the left.
+constexpr int kMR = 8, kMW = 32;
+
+__device__ __forceinline__ uint32_t row_valid_bits(int w, int wpr, int W) {
+    if (w < 0 || w >= wpr)
+        return 0u;
+    const int rem = W - 32 * w;
+    return rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+}
+
+__global__ void __launch_bounds__(kMR * kMW) k_morph_open3(const uint32_t *in, uint32_t *out,
+                                                          int H, int W, int wpr) {
+    __shared__ uint32_t s_in[kMR + 4][kMW + 4];  // rows r0-2.., words w0-2..
+    __shared__ uint32_t s_h[kMR + 4][kMW + 2];   // horizontal erosion, words w0-1..
+    __shared__ uint32_t s_e[kMR + 2][kMW + 2];   // erosion, rows r0-1.., words w0-1..
+    __shared__ uint32_t s_hd[kMR + 2][kMW];      // horizontal dilation, words w0..
+    const int r0 = blockIdx.y * kMR, w0 = blockIdx.x * kMW;
+    const int tid = threadIdx.y * kMW + threadIdx.x, nt = kMR * kMW;
+
+    for (int i = tid; i < (kMR + 4) * (kMW + 4); i += nt) {
+        const int rr = i / (kMW + 4), ww = i % (kMW + 4);
+        const int r = r0 - 2 + rr, w = w0 - 2 + ww;
+        uint32_t v = 0u;
+        if (r >= 0 && r < H && w >= 0 && w < wpr)
+            v = in[(int64_t)r * wpr + w] & row_valid_bits(w, wpr, W);
+        s_in[rr][ww] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < (kMR + 4) * (kMW + 2); i += nt) {
+        const int rr = i / (kMW + 2), ww = i % (kMW + 2);
+        const uint32_t m = s_in[rr][ww + 1], l = s_in[rr][ww], r = s_in[rr][ww + 2];
+        s_h[rr][ww] = m & ((m << 1) | (l >> 31)) & ((m >> 1) | (r << 31));
+    }
+    __syncthreads();
+    for (int i = tid; i < (kMR + 2) * (kMW + 2); i += nt) {
+        const int rr = i / (kMW + 2), ww = i % (kMW + 2);
+        const int r = r0 - 1 + rr, w = w0 - 1 + ww;
+        uint32_t e = s_h[rr][ww] & s_h[rr + 1][ww] & s_h[rr + 2][ww];
+        if (r < 0 || r >= H)
+            e = 0u;
+        s_e[rr][ww] = e & row_valid_bits(w, wpr, W);
+    }
+    __syncthreads();
+    for (int i = tid; i < (kMR + 2) * kMW; i += nt) {
+        const int rr = i / kMW, ww = i % kMW;
+        const uint32_t m = s_e[rr][ww + 1], l = s_e[rr][ww], r = s_e[rr][ww + 2];
+        s_hd[rr][ww] = m | (m << 1) | (l >> 31) | (m >> 1) | (r << 31);
+    }
+    __syncthreads();
+    const int r = r0 + threadIdx.y, w = w0 + threadIdx.x;
+    if (r < H && w < wpr) {
+        const int rr = threadIdx.y + 1;
+        const uint32_t o = s_hd[rr - 1][threadIdx.x] | s_hd[rr][threadIdx.x] | s_hd[rr + 1][threadIdx.x];
+        out[(int64_t)r * wpr + w] = o & row_valid_bits(w, wpr, W);
+    }
+}
+
+} // namespace
+
+namespace gmmhost {
+
+cudaError_t launch_tick(const CamView &cv, int threads, cudaStream_t s) {
+    if (cv.n_pad == 0)
+        return cudaSuccess;
+    if (cv.prec == 0) {
+        switch (cv.M) {
+        case 3: return launch_tick_t<3, 0>(cv, threads, s);
+        case 4: return launch_tick_t<4, 0>(cv, threads, s);
+        case 5: return launch_tick_t<5, 0>(cv, threads, s);
+        }
+    } else {
+        switch (cv.M) {
+        case 3: return launch_tick_t<3, 1>(cv, threads, s);
+        case 4: return launch_tick_t<4, 1>(cv, threads, s);
+        case 5: return launch_tick_t<5, 1>(cv, threads, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fuse(const uint32_t *fg_rgb, const uint32_t *fg_d, uint8_t *fusion,
+                        uint32_t *mask, int H, int W, cudaStream_t s) {
+    const int wpr = (W + 31) / 32;
+    const int64_t n_pad = (int64_t)H * wpr * 32;
+    if (n_pad == 0)
+        return cudaSuccess;
+    k_fuse<<<(unsigned)((n_pad + 255) / 256), 256, 0, s>>>(fg_rgb, fg_d, fusion, mask, H, W, wpr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_morph_open3(const uint32_t *in, uint32_t *out, int H, int W, cudaStream_t s) {
+    const int wpr = (W + 31) / 32;
+    dim3 grid((unsigned)((wpr + kMW - 1) / kMW), (unsigned)((H + kMR - 1) / kMR));
+    k_morph_open3<<<grid, dim3(kMW, kMR), 0, s>>>(in, out, H, W, wpr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pool_tick_impl(const PoolArgs &a, int threads, int blocks, int prec,
+                                  cudaStream_t s) {
+    if (prec == 0)
+        k_pool_tick<0><<<blocks, threads, 0, s>>>(a);
+    else
+        k_pool_tick<1><<<blocks, threads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int pool_max_ctas_per_sm(int prec, int threads) {
+    int n = 0;
+    cudaError_t e = prec == 0
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool_tick<0>, threads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool_tick<1>, threads, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n < 1 ? 1 : n;
+}
+
+int num_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 1;
+    return n;
+}
+
+} // namespace gmmhost

@@ -1,0 +1,530 @@
+// Multi-camera pool: resident per-camera models, one persistent launch per
+// tick over every camera with a submitted frame, optional CUDA-graph replay
+// of the tick, and an autotuner for the launch shape.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gmm.h"
+#include "gmm_common.h"
+#include "gmm_internal.h"
+
+using gmmdev::CamView;
+using namespace gmmlib;
+
+namespace {
+
+struct PoolCam {
+    bool used = false;
+    gmm_config cfg{};
+    Layout L{};
+    void *arena = nullptr;
+    int initialized = 0;
+    bool submitted = false;
+    const uint8_t *rgb = nullptr;
+    const uint16_t *depth = nullptr;
+    uint32_t *mask = nullptr, *fgr = nullptr, *fgd = nullptr;
+};
+
+struct GraphSig {
+    int n_jobs = -1, threads = 0, blocks = 0, tile_pixels = 0;
+    int64_t n_tiles = -1;
+    bool operator==(const GraphSig &o) const {
+        return n_jobs == o.n_jobs && threads == o.threads && blocks == o.blocks &&
+               tile_pixels == o.tile_pixels && n_tiles == o.n_tiles;
+    }
+};
+
+constexpr int kStaging = 2;
+
+} // namespace
+
+namespace gmmhost {
+int pool_max_ctas_per_sm(int prec, int threads);
+}
+
+struct gmm_pool {
+    size_t budget = 0, used_bytes = 0;
+    int prec = 0, max_cams = 0, device = 0;
+    std::vector<PoolCam> cams;
+    cudaStream_t stream = nullptr;
+    cudaError_t sticky = cudaSuccess;
+    int threads = 256, ctas_per_sm = 0, tile_pixels = 4096;
+    CamView *d_views = nullptr;
+    int64_t *d_tile_begin = nullptr;
+    int *d_counter = nullptr;
+    CamView *h_views[kStaging] = {};
+    int64_t *h_tile_begin[kStaging] = {};
+    cudaEvent_t ev_staged[kStaging] = {};
+    bool staged_used[kStaging] = {};
+    int buf = 0;
+    bool use_graph = false;
+    cudaGraphExec_t gexec[kStaging] = {};
+    GraphSig gsig[kStaging];
+};
+
+static void destroy_graphs(gmm_pool *p) {
+    for (int b = 0; b < kStaging; ++b) {
+        if (p->gexec[b])
+            cudaGraphExecDestroy(p->gexec[b]);
+        p->gexec[b] = nullptr;
+        p->gsig[b] = GraphSig();
+    }
+}
+
+static int blocks_for(const gmm_pool *p) {
+    int per_sm = p->ctas_per_sm;
+    const int max_per_sm = gmmhost::pool_max_ctas_per_sm(p->prec, p->threads);
+    if (per_sm <= 0 || per_sm > max_per_sm)
+        per_sm = max_per_sm;
+    if (per_sm < 1)
+        per_sm = 1;
+    return gmmhost::num_sms() * per_sm;
+}
+
+// Enqueue the tick's table uploads, counter reset and the persistent launch.
+static cudaError_t enqueue_body(gmm_pool *p, int b, int n_jobs, int64_t n_tiles, int blocks) {
+    cudaError_t e = cudaMemcpyAsync(p->d_views, p->h_views[b], sizeof(CamView) * n_jobs,
+                                    cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_tile_begin, p->h_tile_begin[b], sizeof(int64_t) * (n_jobs + 1),
+                            cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), p->stream);
+    if (e != cudaSuccess)
+        return e;
+    gmmhost::PoolArgs a;
+    a.views = p->d_views;
+    a.tile_begin = p->d_tile_begin;
+    a.counter = p->d_counter;
+    a.n_jobs = n_jobs;
+    a.tile_pixels = p->tile_pixels;
+    a.n_tiles = n_tiles;
+    return gmmhost::launch_pool_tick_impl(a, p->threads, blocks, p->prec, p->stream);
+}
+
+// One tick over the submitted cameras. clear: drop the submissions and mark
+// the cameras initialised afterwards (false while autotuning).
+static int pool_tick_impl(gmm_pool *p, bool clear) {
+    int n_jobs = 0;
+    for (const PoolCam &c : p->cams)
+        n_jobs += (c.used && c.submitted) ? 1 : 0;
+    if (n_jobs == 0)
+        return GMM_OK;
+    const int b = p->buf;
+    if (p->staged_used[b]) {
+        // The upload that last read this staging buffer must have run.
+        const int rc = wait_event(p->ev_staged[b], 60000, &p->sticky, "gmm_pool_tick staging");
+        if (rc != GMM_OK)
+            return rc;
+    }
+    int j = 0;
+    int64_t tiles = 0;
+    for (PoolCam &c : p->cams) {
+        if (!(c.used && c.submitted))
+            continue;
+        p->h_views[b][j] = make_view(c.cfg, c.L, c.arena, c.rgb, c.depth, c.mask, c.fgr, c.fgd,
+                                     c.initialized ? 0 : 1);
+        p->h_tile_begin[b][j] = tiles;
+        tiles += (c.L.n_pad + p->tile_pixels - 1) / p->tile_pixels;
+        ++j;
+    }
+    p->h_tile_begin[b][n_jobs] = tiles;
+    const int blocks = blocks_for(p);
+    cudaError_t e = cudaSuccess;
+    if (p->use_graph) {
+        GraphSig sig;
+        sig.n_jobs = n_jobs;
+        sig.threads = p->threads;
+        sig.blocks = blocks;
+        sig.tile_pixels = p->tile_pixels;
+        sig.n_tiles = tiles;
+        if (!(p->gexec[b] && p->gsig[b] == sig)) {
+            if (p->gexec[b])
+                cudaGraphExecDestroy(p->gexec[b]);
+            p->gexec[b] = nullptr;
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t eb = enqueue_body(p, b, n_jobs, tiles, blocks);
+                e = cudaStreamEndCapture(p->stream, &g);
+                if (eb != cudaSuccess)
+                    e = eb;
+            }
+            if (e == cudaSuccess)
+                e = cudaGraphInstantiate(&p->gexec[b], g, 0);
+            if (g)
+                cudaGraphDestroy(g);
+            if (e == cudaSuccess)
+                p->gsig[b] = sig;
+        }
+        if (e == cudaSuccess)
+            e = cudaGraphLaunch(p->gexec[b], p->stream);
+    } else {
+        e = enqueue_body(p, b, n_jobs, tiles, blocks);
+    }
+    if (e == cudaSuccess)
+        e = cudaEventRecord(p->ev_staged[b], p->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(&p->sticky, e, "gmm_pool_tick");
+    p->staged_used[b] = true;
+    p->buf = (b + 1) % kStaging;
+    if (clear) {
+        for (PoolCam &c : p->cams) {
+            if (c.used && c.submitted) {
+                c.initialized = 1;
+                c.submitted = false;
+            }
+        }
+    }
+    return GMM_OK;
+}
+
+static bool valid_cam(const gmm_pool *p, int cam) {
+    return p && cam >= 0 && cam < (int)p->cams.size() && p->cams[cam].used;
+}
+
+extern "C" {
+
+gmm_pool_t *gmm_pool_create(size_t budget_bytes, int precision, int max_cams) {
+    if (precision != GMM_PREC_F32 && precision != GMM_PREC_F16) {
+        fail(GMM_EINVAL, "gmm_pool_create: bad precision");
+        return nullptr;
+    }
+    if (max_cams < 1 || max_cams > 65536) {
+        fail(GMM_EINVAL, "gmm_pool_create: max_cams must be in [1, 65536]");
+        return nullptr;
+    }
+    gmm_pool *p = new (std::nothrow) gmm_pool();
+    if (!p) {
+        fail(GMM_ENOMEM, "gmm_pool_create: host allocation failed");
+        return nullptr;
+    }
+    p->budget = budget_bytes;
+    p->prec = precision;
+    p->max_cams = max_cams;
+    p->cams.resize((size_t)max_cams);
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&p->d_views, sizeof(CamView) * (size_t)max_cams);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&p->d_tile_begin, sizeof(int64_t) * ((size_t)max_cams + 1));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&p->d_counter, sizeof(int));
+    for (int b = 0; b < kStaging && e == cudaSuccess; ++b) {
+        e = cudaMallocHost(&p->h_views[b], sizeof(CamView) * (size_t)max_cams);
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&p->h_tile_begin[b], sizeof(int64_t) * ((size_t)max_cams + 1));
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&p->ev_staged[b], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        fail(e == cudaErrorMemoryAllocation ? GMM_ENOMEM : GMM_ECUDA,
+             std::string("gmm_pool_create: ") + cudaGetErrorString(e));
+        cudaGetLastError();
+        gmm_pool_destroy(p);
+        return nullptr;
+    }
+    return p;
+}
+
+int gmm_pool_admit(gmm_pool_t *p, const gmm_config *cfg) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_admit: null pool");
+    const std::string msg = check_config(cfg);
+    if (!msg.empty())
+        return fail(GMM_EINVAL, "gmm_pool_admit: " + msg);
+    if (cfg->precision != p->prec)
+        return fail(GMM_EINVAL, "gmm_pool_admit: precision differs from the pool's");
+    if (cfg->morph_open)
+        return fail(GMM_EINVAL, "gmm_pool_admit: morph_open is not supported in a pool");
+    const Layout L = make_layout(cfg->H, cfg->W, cfg->M, cfg->precision);
+    if (p->budget && p->used_bytes + L.total > p->budget)
+        return fail(GMM_EBUDGET, "gmm_pool_admit: state budget exhausted");
+    int slot = -1;
+    for (int i = 0; i < (int)p->cams.size(); ++i)
+        if (!p->cams[i].used) {
+            slot = i;
+            break;
+        }
+    if (slot < 0)
+        return fail(GMM_ENOMEM, "gmm_pool_admit: every slot is taken");
+    DeviceGuard g(p->device);
+    void *arena = nullptr;
+    cudaError_t e = cudaMallocAsync(&arena, L.total, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(arena, 0, L.total, p->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (arena)
+            cudaFreeAsync(arena, p->stream);
+        return fail(e == cudaErrorMemoryAllocation ? GMM_ENOMEM : GMM_ECUDA,
+                    std::string("gmm_pool_admit: ") + cudaGetErrorString(e));
+    }
+    PoolCam &c = p->cams[slot];
+    c = PoolCam();
+    c.used = true;
+    c.cfg = *cfg;
+    c.L = L;
+    c.arena = arena;
+    p->used_bytes += L.total;
+    return slot;
+}
+
+int gmm_pool_release(gmm_pool_t *p, int cam) {
+    if (!valid_cam(p, cam))
+        return fail(GMM_EINVAL, "gmm_pool_release: unknown camera");
+    DeviceGuard g(p->device);
+    PoolCam &c = p->cams[cam];
+    // Stream-ordered free: queued ticks that use the state run first.
+    const cudaError_t e = cudaFreeAsync(c.arena, p->stream);
+    p->used_bytes -= c.L.total;
+    c = PoolCam();
+    if (e != cudaSuccess)
+        return cuda_fail(&p->sticky, e, "gmm_pool_release");
+    return GMM_OK;
+}
+
+int gmm_pool_submit(gmm_pool_t *p, int cam, const uint8_t *rgb8, const uint16_t *depth16,
+                    uint32_t *mask_out, uint32_t *fg_rgb_out, uint32_t *fg_d_out) {
+    if (!valid_cam(p, cam))
+        return fail(GMM_EINVAL, "gmm_pool_submit: unknown camera");
+    const std::string msg = check_frame_ptrs(rgb8, depth16, mask_out, fg_rgb_out, fg_d_out);
+    if (!msg.empty())
+        return fail(GMM_EINVAL, "gmm_pool_submit: " + msg);
+    PoolCam &c = p->cams[cam];
+    c.submitted = true;
+    c.rgb = rgb8;
+    c.depth = depth16;
+    c.mask = mask_out;
+    c.fgr = fg_rgb_out;
+    c.fgd = fg_d_out;
+    return GMM_OK;
+}
+
+int gmm_pool_tick(gmm_pool_t *p) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_tick: null pool");
+    if (p->sticky != cudaSuccess)
+        return fail(GMM_ECUDA, std::string("gmm_pool_tick: earlier CUDA failure: ") +
+                                   cudaGetErrorString(p->sticky));
+    DeviceGuard g(p->device);
+    return pool_tick_impl(p, true);
+}
+
+int gmm_pool_set_stream(gmm_pool_t *p, void *cuda_stream) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_set_stream: null pool");
+    if (p->stream != static_cast<cudaStream_t>(cuda_stream))
+        destroy_graphs(p);
+    p->stream = static_cast<cudaStream_t>(cuda_stream);
+    return GMM_OK;
+}
+
+int gmm_pool_set_launch(gmm_pool_t *p, int threads, int ctas_per_sm, int tile_pixels) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_set_launch: null pool");
+    const int t = threads ? threads : p->threads;
+    const int c = ctas_per_sm ? ctas_per_sm : p->ctas_per_sm;
+    const int tp = tile_pixels ? tile_pixels : p->tile_pixels;
+    if (t < 64 || t > 512 || t % 32)
+        return fail(GMM_EINVAL, "gmm_pool_set_launch: threads must be 64..512, a multiple of 32");
+    if (c < 0 || c > 32)
+        return fail(GMM_EINVAL, "gmm_pool_set_launch: ctas_per_sm must be in [0, 32]");
+    if (tp < t || tp % t || tp > (1 << 24))
+        return fail(GMM_EINVAL, "gmm_pool_set_launch: tile_pixels must be a multiple of threads");
+    p->threads = t;
+    p->ctas_per_sm = c;
+    p->tile_pixels = tp;
+    return GMM_OK;
+}
+
+int gmm_pool_use_graph(gmm_pool_t *p, int enable) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_use_graph: null pool");
+    p->use_graph = enable != 0;
+    if (!p->use_graph)
+        destroy_graphs(p);
+    return GMM_OK;
+}
+
+int gmm_pool_autotune(gmm_pool_t *p, int iters, int *threads_out, int *ctas_out,
+                      int *tile_out) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_autotune: null pool");
+    if (iters < 1)
+        return fail(GMM_EINVAL, "gmm_pool_autotune: iters must be >= 1");
+    if (p->sticky != cudaSuccess)
+        return fail(GMM_ECUDA, "gmm_pool_autotune: earlier CUDA failure");
+    bool any = false;
+    size_t snap_bytes = 0;
+    for (const PoolCam &c : p->cams)
+        if (c.used && c.submitted) {
+            any = true;
+            snap_bytes += c.L.total;
+        }
+    if (!any)
+        return fail(GMM_EINVAL, "gmm_pool_autotune: no camera has a submitted frame");
+    DeviceGuard g(p->device);
+    // Snapshot every submitted camera's state so the trials leave no trace.
+    uint8_t *snap = nullptr;
+    cudaError_t e = cudaMalloc(&snap, snap_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GMM_ENOMEM, "gmm_pool_autotune: no room for the state snapshot");
+    }
+    std::vector<int> init_saved(p->cams.size());
+    size_t off = 0;
+    for (size_t i = 0; i < p->cams.size() && e == cudaSuccess; ++i) {
+        PoolCam &c = p->cams[i];
+        init_saved[i] = c.initialized;
+        if (c.used && c.submitted) {
+            e = cudaMemcpyAsync(snap + off, c.arena, c.L.total, cudaMemcpyDeviceToDevice, p->stream);
+            off += c.L.total;
+        }
+    }
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&t0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&t1);
+    const int saved_t = p->threads, saved_c = p->ctas_per_sm, saved_tp = p->tile_pixels;
+    const bool saved_graph = p->use_graph;
+    p->use_graph = false;
+    int best_t = saved_t, best_c = saved_c, best_tp = saved_tp;
+    float best_ms = -1.f;
+    const int cand_threads[] = {128, 256, 512};
+    const int cand_tiles[] = {2048, 8192, 32768};
+    int rc = GMM_OK;
+    for (int t : cand_threads) {
+        const int max_c = gmmhost::pool_max_ctas_per_sm(p->prec, t);
+        int cand_c[2] = {max_c, max_c > 1 ? max_c / 2 : 0};
+        for (int c : cand_c) {
+            if (c < 1)
+                continue;
+            for (int tp : cand_tiles) {
+                if (e != cudaSuccess || rc != GMM_OK)
+                    break;
+                p->threads = t;
+                p->ctas_per_sm = c;
+                p->tile_pixels = tp;
+                rc = pool_tick_impl(p, false); // warm-up of this shape
+                if (rc != GMM_OK)
+                    break;
+                e = cudaEventRecord(t0, p->stream);
+                for (int k = 0; k < iters && rc == GMM_OK; ++k)
+                    rc = pool_tick_impl(p, false);
+                if (e == cudaSuccess)
+                    e = cudaEventRecord(t1, p->stream);
+                if (e == cudaSuccess)
+                    e = cudaEventSynchronize(t1);
+                float ms = 0.f;
+                if (e == cudaSuccess)
+                    e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e == cudaSuccess && rc == GMM_OK && (best_ms < 0.f || ms < best_ms)) {
+                    best_ms = ms;
+                    best_t = t;
+                    best_c = c;
+                    best_tp = tp;
+                }
+                for (PoolCam &cam : p->cams)
+                    if (cam.used && cam.submitted)
+                        cam.initialized = 1; // later trials update, as real ticks would
+            }
+        }
+    }
+    // Restore the snapshot and the initialisation flags.
+    off = 0;
+    for (size_t i = 0; i < p->cams.size(); ++i) {
+        PoolCam &c = p->cams[i];
+        c.initialized = init_saved[i];
+        if (c.used && c.submitted) {
+            const cudaError_t er = cudaMemcpyAsync(c.arena, snap + off, c.L.total,
+                                                   cudaMemcpyDeviceToDevice, p->stream);
+            if (e == cudaSuccess)
+                e = er;
+            off += c.L.total;
+        }
+    }
+    const cudaError_t es = cudaStreamSynchronize(p->stream);
+    if (e == cudaSuccess)
+        e = es;
+    cudaFree(snap);
+    if (t0)
+        cudaEventDestroy(t0);
+    if (t1)
+        cudaEventDestroy(t1);
+    p->use_graph = saved_graph;
+    if (e != cudaSuccess)
+        return cuda_fail(&p->sticky, e, "gmm_pool_autotune");
+    if (rc != GMM_OK)
+        return rc;
+    p->threads = best_t;
+    p->ctas_per_sm = best_c;
+    p->tile_pixels = best_tp;
+    destroy_graphs(p);
+    if (threads_out)
+        *threads_out = best_t;
+    if (ctas_out)
+        *ctas_out = best_c;
+    if (tile_out)
+        *tile_out = best_tp;
+    return GMM_OK;
+}
+
+int gmm_pool_state_get(const gmm_pool_t *p, int cam, int plane, int component,
+                       float *dst_host, size_t n) {
+    if (!valid_cam(p, cam))
+        return fail(GMM_EINVAL, "gmm_pool_state_get: unknown camera");
+    DeviceGuard g(p->device);
+    gmm_pool *pm = const_cast<gmm_pool *>(p);
+    const PoolCam &c = p->cams[cam];
+    return state_get_common(c.cfg, c.L, c.arena, p->stream, &pm->sticky, plane, component,
+                            dst_host, n);
+}
+
+size_t gmm_pool_state_used(const gmm_pool_t *p) { return p ? p->used_bytes : 0; }
+
+int gmm_pool_sync(gmm_pool_t *p) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_sync: null pool");
+    DeviceGuard g(p->device);
+    const cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(&p->sticky, e, "gmm_pool_sync");
+    return p->sticky == cudaSuccess ? GMM_OK : fail(GMM_ECUDA, "gmm_pool_sync: earlier CUDA failure");
+}
+
+int gmm_pool_destroy(gmm_pool_t *p) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_destroy: null pool");
+    DeviceGuard g(p->device);
+    cudaStreamSynchronize(p->stream);
+    destroy_graphs(p);
+    for (PoolCam &c : p->cams)
+        if (c.used && c.arena)
+            cudaFreeAsync(c.arena, p->stream);
+    cudaStreamSynchronize(p->stream);
+    if (p->d_views)
+        cudaFree(p->d_views);
+    if (p->d_tile_begin)
+        cudaFree(p->d_tile_begin);
+    if (p->d_counter)
+        cudaFree(p->d_counter);
+    for (int b = 0; b < kStaging; ++b) {
+        if (p->h_views[b])
+            cudaFreeHost(p->h_views[b]);
+        if (p->h_tile_begin[b])
+            cudaFreeHost(p->h_tile_begin[b]);
+        if (p->ev_staged[b])
+            cudaEventDestroy(p->ev_staged[b]);
+    }
+    delete p;
+    return GMM_OK;
+}
+
+} // extern "C"

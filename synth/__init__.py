@@ -95,6 +95,10 @@ def host_lib():
             L.synth_frames_host.argtypes = [ctypes.POINTER(Scene), ctypes.c_int, ctypes.c_int,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             L.synth_frames_host.restype = ctypes.c_int
+            L.synth_rows_host.argtypes = [ctypes.POINTER(Scene), ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]
+            L.synth_rows_host.restype = ctypes.c_int
             if L.synth_scene_size() != ctypes.sizeof(Scene):
                 raise RuntimeError("synth_scene layout mismatch")
             _host = L
@@ -134,6 +138,19 @@ def frames_host(s: Scene, f0: int, nf: int):
                                       depth.ctypes.data, gt.ctypes.data)
     if rc != 0:
         raise RuntimeError("synth_frames_host failed")
+    return rgb, depth, gt
+
+
+def rows_host(s: Scene, f0: int, nf: int, y0: int, rows: int):
+    """Rows y0..y0+rows-1 of frames f0..f0+nf-1 (same bytes as frames_host)."""
+    W = s.W
+    rgb = np.empty((nf, rows, W, 3), np.uint8)
+    depth = np.empty((nf, rows, W), np.uint16)
+    gt = np.empty((nf, rows, W), np.uint8)
+    rc = host_lib().synth_rows_host(ctypes.byref(s), f0, nf, y0, rows, rgb.ctypes.data,
+                                    depth.ctypes.data, gt.ctypes.data)
+    if rc != 0:
+        raise ValueError("bad row range")
     return rgb, depth, gt
 
 

@@ -92,24 +92,35 @@ int synth_scene_init(synth_scene *s, uint64_t seed, int H, int W, int kind)
     return 0;
 }
 
-/* Frames f0 .. f0+nf-1 into caller buffers: rgb [nf][H][W][3], depth
- * [nf][H][W], gt [nf][H][W] (gt may be NULL). */
-int synth_frames_host(const synth_scene *s, int f0, int nf, uint8_t *rgb,
-                      uint16_t *depth, uint8_t *gt)
+/* Rows y0 .. y0+rows-1 of frames f0 .. f0+nf-1 into caller buffers: rgb
+ * [nf][rows][W][3], depth [nf][rows][W], gt [nf][rows][W] (gt may be NULL). */
+int synth_rows_host(const synth_scene *s, int f0, int nf, int y0, int rows,
+                    uint8_t *rgb, uint16_t *depth, uint8_t *gt)
 {
-    if (!s || !rgb || !depth || nf < 0 || f0 < 0)
+    if (!s || !rgb || !depth || nf < 0 || f0 < 0 || y0 < 0 || rows < 0 ||
+        y0 + rows > s->H)
         return -1;
-    const int64_t N = (int64_t)s->H * s->W;
+    const int64_t N = (int64_t)rows * s->W;
     for (int f = 0; f < nf; f++) {
-        for (int32_t y = 0; y < s->H; y++) {
+        for (int32_t r = 0; r < rows; r++) {
             for (int32_t x = 0; x < s->W; x++) {
-                int64_t n = (int64_t)f * N + (int64_t)y * s->W + x;
+                int64_t n = (int64_t)f * N + (int64_t)r * s->W + x;
                 uint8_t g;
-                synth_pixel(s, f0 + f, x, y, rgb + 3 * n, depth + n, &g);
+                synth_pixel(s, f0 + f, x, y0 + r, rgb + 3 * n, depth + n, &g);
                 if (gt)
                     gt[n] = g;
             }
         }
     }
     return 0;
+}
+
+/* Whole frames f0 .. f0+nf-1: rgb [nf][H][W][3], depth [nf][H][W], gt
+ * [nf][H][W] (gt may be NULL). */
+int synth_frames_host(const synth_scene *s, int f0, int nf, uint8_t *rgb,
+                      uint16_t *depth, uint8_t *gt)
+{
+    if (!s)
+        return -1;
+    return synth_rows_host(s, f0, nf, 0, s->H, rgb, depth, gt);
 }

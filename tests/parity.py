@@ -1,0 +1,109 @@
+"""Side-by-side runs of the CUDA path and the FP64 oracle on the same seeded
+synthetic frames, and the comparison rules.
+
+Tolerances (the spec contract for this path):
+  - state: |gpu - oracle| <= 1e-4 * max(|oracle|, floor), floors 1e-3 for
+    weights, 1 for means and variances (FP32 state);
+  - masks: bit-exact, except pixels where the oracle flags a decision within
+    1e-5 relative of its threshold at that tick (match distance vs k^2 v,
+    rank-prefix weight vs T, two sort keys); those are counted and reported.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+import paper_2110_14934_gb300 as G
+import synth
+
+RTOL = 1e-4
+FLOORS = np.array([1e-3, 1.0, 1.0, 1.0, 1.0, 1e-3, 1.0, 1.0])  # per plane, PLANES order
+DEFAULTS = dict(alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0, init_w=0.05)
+
+
+def to_dev(rgb, depth):
+    import torch
+    r = torch.from_numpy(np.ascontiguousarray(rgb)).cuda()
+    d = torch.from_numpy(np.ascontiguousarray(depth).view(np.int16)).cuda()
+    return r, d
+
+
+def words(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint32)
+
+
+class Pair:
+    """A GPU model and an oracle model with the same parameters."""
+
+    def __init__(self, H, W, M, precision=G.PREC_F32, **kw):
+        p = dict(DEFAULTS)
+        p.update(kw)
+        self.H, self.W, self.M = H, W, M
+        self.gpu = G.GMM(H, W, M, precision=precision, **p)
+        self.orc = O.OracleGMM(H, W, M, p["alpha"], p["match_k"], p["bg_T"], p["init_var"],
+                               p["init_w"], init_var_d=p.get("init_var_d"),
+                               v_min_c=p.get("v_min_c", 1.0), v_min_d=p.get("v_min_d", 1.0))
+
+    def tick(self, rgb, depth):
+        """One tick on both; returns (gpu dict of bool masks, oracle dict)."""
+        import torch
+        r, d = to_dev(rgb, depth)
+        wpr = G.mask_words_per_row(self.W)
+        m = torch.empty((self.H, wpr), dtype=torch.int32, device="cuda")
+        fc = torch.empty_like(m)
+        fd = torch.empty_like(m)
+        self.gpu.apply(r, d, m, fc, fd)
+        torch.cuda.synchronize()
+        g = {"fused": G.unpack_mask(words(m), self.H, self.W),
+             "fg_rgb": G.unpack_mask(words(fc), self.H, self.W),
+             "fg_d": G.unpack_mask(words(fd), self.H, self.W)}
+        o = self.orc.tick(rgb, depth)
+        return g, o
+
+    def sync_oracle_to_gpu(self):
+        """Teacher forcing: the oracle continues from the GPU's exact state."""
+        self.orc.set_state(self.gpu.planes().astype(np.float64), self.gpu.fusion())
+
+    def load_gpu_from_oracle(self):
+        """Load the oracle's state (rounded to the storage type) into the GPU
+        and round the oracle's copy the same way, so both start equal."""
+        planes = self.orc.planes()
+        fusion = self.orc.fusion_bytes()
+        self.gpu.load_state(planes.astype(np.float32), fusion)
+        self.orc.set_state(self.gpu.planes().astype(np.float64), self.gpu.fusion())
+
+
+def mask_mismatch(g: dict, o: dict, exempt: np.ndarray) -> dict:
+    out = {}
+    for k in ("fused", "fg_rgb", "fg_d"):
+        diff = g[k] != o[k].astype(bool)
+        out[k] = int(np.count_nonzero(diff & ~exempt))
+        out[k + "_exempt"] = int(np.count_nonzero(diff & exempt))
+    return out
+
+
+def state_mismatch(gpu_planes, orc_planes, orc_fusion, exclude=None, rtol=RTOL, floors=FLOORS):
+    """Counts of state values outside tolerance, per plane; depth planes are
+    compared only where the depth model has started."""
+    M = gpu_planes.shape[0]
+    dstarted = ((orc_fusion >> 4) & 1).astype(bool)
+    bad = np.zeros(8, dtype=np.int64)
+    worst = np.zeros(8)
+    for f in range(8):
+        o = orc_planes[:, f]
+        gg = gpu_planes[:, f].astype(np.float64)
+        err = np.abs(gg - o) / np.maximum(np.abs(o), floors[f])
+        valid = np.ones_like(err, dtype=bool)
+        if f >= 5:
+            valid &= dstarted[None]
+        if exclude is not None:
+            valid &= ~exclude[None]
+        e = np.where(valid, err, 0.0)
+        worst[f] = e.max() if e.size else 0.0
+        bad[f] = int(np.count_nonzero(e > rtol))
+    return {"bad": bad.tolist(), "worst": worst.tolist(), "components": M}
+
+
+def scene_frames(seed, H, W, kind, f0, nf):
+    s = synth.scene(seed, H, W, kind)
+    return synth.frames_host(s, f0, nf)

@@ -1,0 +1,114 @@
+"""The C-ABI library on a machine without a GPU: it builds and loads, exports
+every function include/gmm.h declares, and rejects bad arguments on the host
+before touching the device. No compute call is made here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2110_14934_gb300 as G
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(gmm_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    L = G.load_library()
+    names = declared_functions()
+    assert len(names) >= 30
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_config_defaults():
+    L = G.load_library()
+    cfg = G.GMMConfig()
+    L.gmm_config_init(ctypes.byref(cfg), 480, 640, 3, 0.01, 2.5, 0.7, 225.0, 0.05)
+    assert (cfg.H, cfg.W, cfg.M) == (480, 640, 3)
+    assert cfg.init_var_d == np.float32(225.0) and cfg.v_min_c == 1.0 and cfg.v_min_d == 1.0
+    assert cfg.precision == G.PREC_F32 and cfg.morph_open == 0
+
+
+@pytest.mark.parametrize("args,frag", [
+    ((0, 640, 3, 0.01, 2.5, 0.7, 225.0, 0.05), "H and W"),
+    ((480, 0, 3, 0.01, 2.5, 0.7, 225.0, 0.05), "H and W"),
+    ((480, 640, 2, 0.01, 2.5, 0.7, 225.0, 0.05), "M must be in [3, 5]"),
+    ((480, 640, 6, 0.01, 2.5, 0.7, 225.0, 0.05), "M must be in [3, 5]"),
+    ((480, 640, 3, 0.0, 2.5, 0.7, 225.0, 0.05), "alpha"),
+    ((480, 640, 3, 1.0, 2.5, 0.7, 225.0, 0.05), "alpha"),
+    ((480, 640, 3, float("nan"), 2.5, 0.7, 225.0, 0.05), "alpha"),
+    ((480, 640, 3, 0.01, 0.0, 0.7, 225.0, 0.05), "match_k"),
+    ((480, 640, 3, 0.01, float("inf"), 0.7, 225.0, 0.05), "match_k"),
+    ((480, 640, 3, 0.01, 2.5, 1.0, 225.0, 0.05), "bg_T"),
+    ((480, 640, 3, 0.01, 2.5, 0.0, 225.0, 0.05), "bg_T"),
+    ((480, 640, 3, 0.01, 2.5, 0.7, 0.0, 0.05), "init_var"),
+    ((480, 640, 3, 0.01, 2.5, 0.7, 225.0, 0.0), "init_w"),
+    ((480, 640, 3, 0.01, 2.5, 0.7, 225.0, 1.0), "init_w"),
+    ((1 << 16, 1 << 16, 3, 0.01, 2.5, 0.7, 225.0, 0.05), "too large"),
+])
+def test_create_rejects_bad_parameters(args, frag):
+    L = G.load_library()
+    h = L.gmm_create(*args)
+    assert not h
+    assert frag in L.gmm_last_error().decode()
+
+
+def test_create_ex_rejects_bad_extensions():
+    L = G.load_library()
+    cfg = G.GMMConfig()
+    L.gmm_config_init(ctypes.byref(cfg), 48, 64, 4, 0.01, 2.5, 0.7, 225.0, 0.05)
+    for field, val, frag in (("v_min_c", 0.0, "floors"), ("v_min_d", -1.0, "floors"),
+                             ("init_var_d", 0.0, "init_var_d"), ("precision", 7, "precision"),
+                             ("morph_open", 2, "morph_open")):
+        c = G.GMMConfig.from_buffer_copy(cfg)
+        setattr(c, field, val)
+        assert not L.gmm_create_ex(ctypes.byref(c))
+        assert frag in L.gmm_last_error().decode()
+
+
+def test_null_handles_are_rejected():
+    L = G.load_library()
+    assert L.gmm_apply(None, None, None, None) == G.EINVAL
+    assert L.gmm_state_get(None, 0, 0, None, 0) == G.EINVAL
+    assert L.gmm_destroy(None) == G.EINVAL
+    assert L.gmm_pool_tick(None) == G.EINVAL
+    assert L.gmm_pool_admit(None, None) == G.EINVAL
+    assert L.gmm_fuse_masks(None, None, None, None, 4, 4, None) == G.EINVAL
+    assert L.gmm_morph_open3(None, None, 0, 4, None) == G.EINVAL
+    assert L.gmm_pool_create(0, 3, 4) is None
+    assert L.gmm_pool_create(0, 0, 0) is None
+
+
+def test_sizes():
+    assert [G.mask_words_per_row(w) for w in (1, 31, 32, 33, 640, 1920)] == [1, 1, 1, 2, 20, 60]
+    # FP32: 8 planes * M * 4 bytes per padded pixel (planes 256-byte aligned) + 1 fusion byte
+    n = 480 * 640
+    assert G.state_bytes(480, 640, 3, G.PREC_F32) == 3 * 8 * n * 4 + n
+    assert G.state_bytes(1080, 1920, 5, G.PREC_F16) == 5 * 8 * 1080 * 1920 * 2 + 1080 * 1920
+    assert G.state_bytes(1, 1, 3, G.PREC_F32) == 24 * 128 * 4 + 256
+    assert G.state_bytes(10, 10, 2, G.PREC_F32) == 0
+
+
+def test_mask_pack_roundtrip():
+    rng = np.random.default_rng(0)
+    for H, W in ((1, 1), (3, 33), (7, 64), (5, 100)):
+        m = rng.random((H, W)) < 0.5
+        words = G.pack_mask(m)
+        assert words.shape == (H, G.mask_words_per_row(W))
+        assert np.array_equal(G.unpack_mask(words, H, W), m)
+    # bit i of word c is pixel 32c + i, least significant bit first
+    m = np.zeros((1, 40), bool); m[0, 0] = True; m[0, 33] = True
+    assert G.pack_mask(m).tolist() == [[1, 2]]

@@ -1,0 +1,140 @@
+"""GPU tests of the standalone operators (List 1 alone, 3x3 opening), the
+host-memory paths, the device frame generator and the host-side argument
+checks that must stop bad calls before any launch."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2110_14934_gb300 as G
+import synth
+from parity import Pair, scene_frames, to_dev, words
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fuse_masks_exhaustive_sequences():
+    """Every (colour, depth) sequence of length 6 from both initial labels,
+    one pixel per sequence, stepped through gmm_fuse_masks; bit-exact against
+    List 1 in the oracle."""
+    import torch
+    L = 6
+    seqs = list(itertools.product(range(4), repeat=L))
+    n = 2 * len(seqs)
+    H, W = 1, n
+    F0 = np.array([0] * len(seqs) + [1] * len(seqs))
+    steps = np.array(seqs + seqs)  # [n, L]
+    fusion = torch.from_numpy((F0 | (3 << 1)).astype(np.uint8)).cuda()
+    out = torch.empty((1, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda")
+    Fo = F0.copy(); co = np.zeros(n, int)
+    for t in range(L):
+        rgb_bits = (steps[:, t] >> 1) & 1
+        d_bits = steps[:, t] & 1
+        fr = torch.from_numpy(G.pack_mask(rgb_bits[None].astype(bool)).view(np.int32)).cuda()
+        fd = torch.from_numpy(G.pack_mask(d_bits[None].astype(bool)).view(np.int32)).cuda()
+        G.fuse_masks(fr, fd, fusion, out, H, W)
+        for i in range(n):
+            Fo[i], co[i] = O.fuse(int(rgb_bits[i]), int(d_bits[i]), int(Fo[i]), int(co[i]))
+        torch.cuda.synchronize()
+        got = G.unpack_mask(words(out), H, W)[0]
+        assert np.array_equal(got, Fo.astype(bool)), t
+        fb = fusion.cpu().numpy().astype(int)
+        assert np.array_equal(fb & 1, Fo) and np.array_equal(((fb >> 1) & 7) - 3, co), t
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 40), (5, 1), (9, 13), (33, 65), (100, 1000)])
+def test_morph_open3_matches_oracle(H, W):
+    import torch
+    rng = np.random.default_rng(H * 1000 + W)
+    for p in (0.4, 0.8, 0.97):
+        m = rng.random((H, W)) < p
+        packed = G.pack_mask(m)
+        # garbage in the padding bits must not leak into the result
+        if W % 32:
+            packed[:, -1] |= np.uint32(0xFFFFFFFF) << np.uint32(W % 32)
+        src = torch.from_numpy(packed.view(np.int32)).cuda()
+        dst = torch.zeros_like(src)
+        G.morph_open3(src, dst, H, W)
+        torch.cuda.synchronize()
+        got = G.unpack_mask(words(dst), H, W)
+        assert np.array_equal(got, O.morph_open3(m.astype(np.uint8)).astype(bool))
+        if W % 32:
+            assert not np.any(words(dst)[:, -1] >> np.uint32(W % 32))
+
+
+def test_handle_with_morph_open():
+    import torch
+    H, W, M = 60, 90, 3
+    rgb, depth, _ = scene_frames(21, H, W, 0, 0, 8)
+    plain = G.GMM(H, W, M)
+    opened = G.GMM(H, W, M, morph_open=True)
+    for t in range(8):
+        r, d = to_dev(rgb[t], depth[t])
+        a = plain.apply(r, d)
+        b = opened.apply(r, d)
+        torch.cuda.synchronize()
+        ref = O.morph_open3(G.unpack_mask(words(a), H, W).astype(np.uint8)).astype(bool)
+        assert np.array_equal(G.unpack_mask(words(b), H, W), ref)
+
+
+def test_host_path_and_pipeline_match_device_path():
+    import torch
+    H, W, M = 50, 70, 4
+    rgb, depth, _ = scene_frames(8, H, W, 1, 0, 10)
+    dev = G.GMM(H, W, M)
+    host = G.GMM(H, W, M)
+    pipe = G.GMM(H, W, M)
+    ref = []
+    for t in range(10):
+        r, d = to_dev(rgb[t], depth[t])
+        ref.append(words(dev.apply(r, d)).copy())
+    for t in range(10):
+        assert np.array_equal(host.apply_host(rgb[t], depth[t]), ref[t])
+    # pipelined: pinned buffers, several frames in flight
+    rgb_p = [torch.from_numpy(rgb[t].copy()).pin_memory() for t in range(10)]
+    dep_p = [torch.from_numpy(depth[t].view(np.int16).copy()).pin_memory() for t in range(10)]
+    masks = [torch.zeros((H, G.mask_words_per_row(W)), dtype=torch.int32).pin_memory()
+             for _ in range(10)]
+    tickets = [pipe.pipe_submit(rgb_p[t], dep_p[t], masks[t]) for t in range(10)]
+    for t, tk in enumerate(tickets):
+        pipe.pipe_wait(tk, 10000)
+        assert np.array_equal(masks[t].numpy().view(np.uint32), ref[t]), t
+    assert np.array_equal(dev.planes(), pipe.planes())
+
+
+def test_host_side_checks_reject_bad_calls():
+    """Plain host pointers, misaligned pointers and wrong planes are refused
+    on the host; the handle stays usable afterwards."""
+    import torch
+    H, W = 8, 40
+    g = G.GMM(H, W, 3)
+    L = G.load_library()
+    rgb = np.zeros((H, W, 3), np.uint8); dep = np.zeros((H, W), np.uint16)
+    mask = np.zeros((H, 2), np.uint32)
+    assert L.gmm_apply(g._h, rgb.ctypes.data, dep.ctypes.data, mask.ctypes.data) == G.EINVAL
+    r = torch.zeros((H, W, 3), dtype=torch.uint8, device="cuda")
+    d = torch.zeros((H * W + 1,), dtype=torch.int16, device="cuda")
+    m = torch.zeros((H, 2), dtype=torch.int32, device="cuda")
+    bytes_d = d.view(torch.uint8)
+    assert L.gmm_apply(g._h, r.data_ptr(), bytes_d[1:].data_ptr(), m.data_ptr()) == G.EINVAL
+    assert L.gmm_apply(g._h, r.data_ptr(), d.data_ptr(), m.view(torch.uint8)[2:].data_ptr()) == G.EINVAL
+    out = np.zeros(H * W, np.float32)
+    assert L.gmm_state_get(g._h, 9, 0, out.ctypes.data, out.size) == G.EINVAL
+    assert L.gmm_state_get(g._h, 0, 3, out.ctypes.data, out.size) == G.EINVAL
+    assert L.gmm_state_get(g._h, 0, 0, out.ctypes.data, out.size - 1) == G.EINVAL
+    g.apply(r, d[:H * W].view(H, W))
+    g.sync()
+
+
+def test_device_generator_matches_host():
+    import torch
+    for seed, H, W, kind in ((1, 48, 64, 0), (2, 37, 51, 1), (3, 1080, 1920, 1)):
+        s = synth.scene(seed, H, W, kind)
+        f0 = 45
+        rgb, dep, gt = synth.frames_host(s, f0, 3)
+        rd, dd, gd = synth.frames_device(s, f0, 3)
+        torch.cuda.synchronize()
+        assert np.array_equal(rd.cpu().numpy(), rgb)
+        assert np.array_equal(dd.cpu().numpy().view(np.uint16), dep)
+        assert np.array_equal(gd.cpu().numpy(), gt)

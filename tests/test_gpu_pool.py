@@ -1,0 +1,167 @@
+"""The multi-camera pool: one persistent launch per tick over every camera
+with a submitted frame. Results must equal each camera run alone (same
+kernel arithmetic, so bit-identical), whatever mix of cameras shares a tick,
+and must match the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2110_14934_gb300 as G
+import synth
+from parity import scene_frames, state_mismatch, to_dev, words
+
+pytestmark = pytest.mark.gpu
+
+CAMS = [(45, 83, 3), (64, 96, 5), (33, 40, 4), (1, 1, 3), (120, 160, 5)]
+
+
+def _frames(n):
+    return [scene_frames(500 + i, H, W, i % 2, 0, n) for i, (H, W, M) in enumerate(CAMS)]
+
+
+def _alone(frames, schedule):
+    """Each camera in its own handle, fed only on the ticks it is scheduled."""
+    import torch
+    out = {}
+    for i, (H, W, M) in enumerate(CAMS):
+        g = G.GMM(H, W, M)
+        k = 0
+        for t, active in enumerate(schedule):
+            if i in active:
+                r, d = to_dev(frames[i][0][k], frames[i][1][k])
+                out[(i, t)] = words(g.apply(r, d)).copy()
+                k += 1
+        torch.cuda.synchronize()
+        out[i] = g.planes()
+    return out
+
+
+def _pooled(frames, schedule, graph=False, launch=None, precision=G.PREC_F32):
+    import torch
+    pool = G.Pool(precision=precision, max_cams=8)
+    if graph:
+        pool.use_graph(True)
+    if launch:
+        pool.set_launch(*launch)
+    ids = [pool.admit(H, W, M) for (H, W, M) in CAMS]
+    out = {}
+    pos = [0] * len(CAMS)
+    for t, active in enumerate(schedule):
+        masks = {}
+        for i in active:
+            H, W, M = CAMS[i]
+            r, d = to_dev(frames[i][0][pos[i]], frames[i][1][pos[i]])
+            masks[i] = (torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda"), r, d)
+            pool.submit(ids[i], r, d, masks[i][0])
+            pos[i] += 1
+        pool.tick()
+        torch.cuda.synchronize()
+        for i in active:
+            out[(i, t)] = words(masks[i][0]).copy()
+    for i in range(len(CAMS)):
+        out[i] = pool.planes(ids[i])
+    return out, pool, ids
+
+
+def test_pool_equals_alone_every_tick():
+    n = 12
+    frames = _frames(n)
+    schedule = [set(range(len(CAMS)))] * n
+    a = _alone(frames, schedule)
+    b, _, _ = _pooled(frames, schedule)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_pool_equals_alone_in_a_changing_mix():
+    """Cameras join the tick on different schedules (continuous batching):
+    every camera's masks and state equal its run alone."""
+    n = 14
+    frames = _frames(n)
+    rng = np.random.default_rng(3)
+    schedule = [set(int(i) for i in np.nonzero(rng.random(len(CAMS)) < 0.6)[0]) for _ in range(n)]
+    a = _alone(frames, schedule)
+    b, _, _ = _pooled(frames, schedule)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+
+
+@pytest.mark.parametrize("launch", [(128, 1, 128), (512, 2, 2048), (256, 0, 32768)])
+def test_pool_graph_and_launch_shapes(launch):
+    n = 6
+    frames = _frames(n)
+    schedule = [set(range(len(CAMS)))] * 3 + [{0, 2, 4}] * 3
+    a = _alone(frames, schedule)
+    b, _, _ = _pooled(frames, schedule, graph=True, launch=launch)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_pool_matches_oracle():
+    import torch
+    n = 10
+    frames = _frames(n)
+    pool = G.Pool(max_cams=8)
+    ids = [pool.admit(H, W, M) for (H, W, M) in CAMS]
+    orcs = [O.OracleGMM(H, W, M, 0.01, 2.5, 0.7, 225.0, 0.05) for (H, W, M) in CAMS]
+    diverged = [np.zeros((H, W), bool) for (H, W, M) in CAMS]
+    for t in range(n):
+        masks = []
+        for i, (H, W, M) in enumerate(CAMS):
+            r, d = to_dev(frames[i][0][t], frames[i][1][t])
+            m = torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda")
+            pool.submit(ids[i], r, d, m)
+            masks.append((m, r, d))
+        pool.tick()
+        torch.cuda.synchronize()
+        for i, (H, W, M) in enumerate(CAMS):
+            o = orcs[i].tick(frames[i][0][t], frames[i][1][t])
+            diverged[i] |= o["near"] != 0
+            g = G.unpack_mask(words(masks[i][0]), H, W)
+            assert not np.any((g != o["fused"].astype(bool)) & ~diverged[i]), (i, t)
+    for i in range(len(CAMS)):
+        st = state_mismatch(pool.planes(ids[i]), orcs[i].planes(), orcs[i].fusion_bytes(),
+                            exclude=diverged[i])
+        assert sum(st["bad"]) == 0, (i, st)
+
+
+def test_pool_budget_and_release():
+    per = G.state_bytes(64, 96, 5)
+    pool = G.Pool(budget_bytes=2 * per + 10, max_cams=4)
+    a = pool.admit(64, 96, 5)
+    b = pool.admit(64, 96, 5)
+    with pytest.raises(G.GMMError) as e:
+        pool.admit(64, 96, 5)
+    assert e.value.code == G.EBUDGET
+    assert pool.state_used() == 2 * per
+    pool.release(a)
+    c = pool.admit(64, 96, 5)
+    assert c == a and pool.state_used() == 2 * per
+    pool.release(b)
+    pool.release(c)
+    assert pool.state_used() == 0
+    pool.sync()
+
+
+def test_pool_autotune_leaves_state_unchanged():
+    import torch
+    frames = _frames(4)
+    pool = G.Pool(max_cams=8)
+    ids = [pool.admit(H, W, M) for (H, W, M) in CAMS]
+    keep = []
+    for t in range(2):
+        for i, (H, W, M) in enumerate(CAMS):
+            r, d = to_dev(frames[i][0][t], frames[i][1][t])
+            m = torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda")
+            keep.append((r, d, m))
+            pool.submit(ids[i], r, d, m)
+        if t == 0:
+            pool.tick()
+    before = [pool.planes(c) for c in ids]
+    shape = pool.autotune(iters=2)
+    assert shape["threads"] in (128, 256, 512) and shape["tile_pixels"] % shape["threads"] == 0
+    after = [pool.planes(c) for c in ids]
+    for x, y in zip(before, after):
+        assert np.array_equal(x, y)
+    pool.tick()  # the submission survives the autotuner
+    pool.sync()

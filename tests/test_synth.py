@@ -59,3 +59,13 @@ def test_tiny_shapes(H, W):
     for kind in (0, 1):
         rgb, depth, gt = synth.frames_host(synth.scene(2, H, W, kind), 0, 2)
         assert rgb.shape == (2, H, W, 3) and depth.shape == (2, H, W)
+
+
+def test_row_band_matches_whole_frames():
+    s = synth.scene(4, 40, 50, 1)
+    rgb, dep, gt = synth.frames_host(s, 3, 2)
+    r2, d2, g2 = synth.rows_host(s, 3, 2, 11, 7)
+    assert np.array_equal(r2, rgb[:, 11:18]) and np.array_equal(d2, dep[:, 11:18])
+    assert np.array_equal(g2, gt[:, 11:18])
+    with pytest.raises(ValueError):
+        synth.rows_host(s, 0, 1, 35, 6)

@@ -52,6 +52,7 @@ struct gmm_pool {
     int prec = 0, max_cams = 0, device = 0;
     std::vector<PoolCam> cams;
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr; // graph capture (the legacy stream cannot capture)
     cudaError_t sticky = cudaSuccess;
     int threads = 256, ctas_per_sm = 0, tile_pixels = 4096;
     CamView *d_views = nullptr;
@@ -87,14 +88,15 @@ static int blocks_for(const gmm_pool *p) {
 }
 
 // Enqueue the tick's table uploads, counter reset and the persistent launch.
-static cudaError_t enqueue_body(gmm_pool *p, int b, int n_jobs, int64_t n_tiles, int blocks) {
+static cudaError_t enqueue_body(gmm_pool *p, cudaStream_t s, int b, int n_jobs, int64_t n_tiles,
+                                int blocks) {
     cudaError_t e = cudaMemcpyAsync(p->d_views, p->h_views[b], sizeof(CamView) * n_jobs,
-                                    cudaMemcpyHostToDevice, p->stream);
+                                    cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->d_tile_begin, p->h_tile_begin[b], sizeof(int64_t) * (n_jobs + 1),
-                            cudaMemcpyHostToDevice, p->stream);
+                            cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), p->stream);
+        e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), s);
     if (e != cudaSuccess)
         return e;
     gmmhost::PoolArgs a;
@@ -104,7 +106,7 @@ static cudaError_t enqueue_body(gmm_pool *p, int b, int n_jobs, int64_t n_tiles,
     a.n_jobs = n_jobs;
     a.tile_pixels = p->tile_pixels;
     a.n_tiles = n_tiles;
-    return gmmhost::launch_pool_tick_impl(a, p->threads, blocks, p->prec, p->stream);
+    return gmmhost::launch_pool_tick_impl(a, p->threads, blocks, p->prec, s);
 }
 
 // One tick over the submitted cameras. clear: drop the submissions and mark
@@ -148,10 +150,10 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
                 cudaGraphExecDestroy(p->gexec[b]);
             p->gexec[b] = nullptr;
             cudaGraph_t g = nullptr;
-            e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
+            e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                const cudaError_t eb = enqueue_body(p, b, n_jobs, tiles, blocks);
-                e = cudaStreamEndCapture(p->stream, &g);
+                const cudaError_t eb = enqueue_body(p, p->cap_stream, b, n_jobs, tiles, blocks);
+                e = cudaStreamEndCapture(p->cap_stream, &g);
                 if (eb != cudaSuccess)
                     e = eb;
             }
@@ -165,7 +167,7 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         if (e == cudaSuccess)
             e = cudaGraphLaunch(p->gexec[b], p->stream);
     } else {
-        e = enqueue_body(p, b, n_jobs, tiles, blocks);
+        e = enqueue_body(p, p->stream, b, n_jobs, tiles, blocks);
     }
     if (e == cudaSuccess)
         e = cudaEventRecord(p->ev_staged[b], p->stream);
@@ -215,6 +217,8 @@ gmm_pool_t *gmm_pool_create(size_t budget_bytes, int precision, int max_cams) {
         e = cudaMalloc(&p->d_tile_begin, sizeof(int64_t) * ((size_t)max_cams + 1));
     if (e == cudaSuccess)
         e = cudaMalloc(&p->d_counter, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
     for (int b = 0; b < kStaging && e == cudaSuccess; ++b) {
         e = cudaMallocHost(&p->h_views[b], sizeof(CamView) * (size_t)max_cams);
         if (e == cudaSuccess)
@@ -515,6 +519,8 @@ int gmm_pool_destroy(gmm_pool_t *p) {
         cudaFree(p->d_tile_begin);
     if (p->d_counter)
         cudaFree(p->d_counter);
+    if (p->cap_stream)
+        cudaStreamDestroy(p->cap_stream);
     for (int b = 0; b < kStaging; ++b) {
         if (p->h_views[b])
             cudaFreeHost(p->h_views[b]);

@@ -116,9 +116,12 @@ def test_host_side_checks_reject_bad_calls():
     r = torch.zeros((H, W, 3), dtype=torch.uint8, device="cuda")
     d = torch.zeros((H * W + 1,), dtype=torch.int16, device="cuda")
     m = torch.zeros((H, 2), dtype=torch.int32, device="cuda")
-    bytes_d = d.view(torch.uint8)
+    bytes_d = d.view(torch.uint8).reshape(-1)
+    bytes_m = m.view(torch.uint8).reshape(-1)
+    assert (bytes_d[1:].data_ptr() - d.data_ptr()) == 1
+    assert (bytes_m[2:].data_ptr() - m.data_ptr()) == 2
     assert L.gmm_apply(g._h, r.data_ptr(), bytes_d[1:].data_ptr(), m.data_ptr()) == G.EINVAL
-    assert L.gmm_apply(g._h, r.data_ptr(), d.data_ptr(), m.view(torch.uint8)[2:].data_ptr()) == G.EINVAL
+    assert L.gmm_apply(g._h, r.data_ptr(), d.data_ptr(), bytes_m[2:].data_ptr()) == G.EINVAL
     out = np.zeros(H * W, np.float32)
     assert L.gmm_state_get(g._h, 9, 0, out.ctypes.data, out.size) == G.EINVAL
     assert L.gmm_state_get(g._h, 0, 3, out.ctypes.data, out.size) == G.EINVAL

@@ -8,7 +8,7 @@ import pytest
 import oracle as O
 import paper_2110_14934_gb300 as G
 import synth
-from parity import scene_frames, state_mismatch, to_dev, words
+from parity import FREE_RUN_EPS, scene_frames, state_mismatch, to_dev, words
 
 pytestmark = pytest.mark.gpu
 
@@ -103,7 +103,8 @@ def test_pool_matches_oracle():
     frames = _frames(n)
     pool = G.Pool(max_cams=8)
     ids = [pool.admit(H, W, M) for (H, W, M) in CAMS]
-    orcs = [O.OracleGMM(H, W, M, 0.01, 2.5, 0.7, 225.0, 0.05) for (H, W, M) in CAMS]
+    orcs = [O.OracleGMM(H, W, M, 0.01, 2.5, 0.7, 225.0, 0.05, eps=FREE_RUN_EPS)
+            for (H, W, M) in CAMS]
     diverged = [np.zeros((H, W), bool) for (H, W, M) in CAMS]
     for t in range(n):
         masks = []

@@ -203,6 +203,41 @@ int gmm_fuse_masks(const uint32_t *fg_rgb, const uint32_t *fg_d,
 int gmm_morph_open3(const uint32_t *mask_in, uint32_t *mask_out, int H, int W,
                     void *stream);
 
+/* ------------------------------------------------- allocation-free variant */
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory, such as a host application that
+ * reserves all of the GPU's memory at start-up and hands out pieces of it,
+ * a real-time loop that may not stall on the allocator, or code that runs
+ * where allocation calls are not allowed. It performs one tick followed by
+ * the 3x3 opening (what gmm_apply does for a handle created with
+ * morph_open = 1) without any handle and without calling cudaMalloc,
+ * cudaFree or any allocating routine.
+ *
+ * The caller provides the model state: `state` is device memory of
+ * gmm_state_bytes(H, W, M, precision) bytes, 16-byte aligned, laid out as
+ * M*8 planes (plane 8*i + GMM_PLANE_*, i the rank) of S elements each,
+ * S = H*ceil(W/32)*32 rounded up to a multiple of 128, rows padded to a
+ * multiple of 32 pixels, followed by the per-pixel List-1 bytes. The state
+ * persists between calls; first = 1 initialises it from this frame (it
+ * need not be cleared beforehand), first = 0 updates it. cfg gives the
+ * model parameters (its morph_open field is ignored). rgb8, depth16 and
+ * mask_out are as for gmm_apply; mask_out receives the opened mask.
+ * Asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream).
+ *
+ * The fused mask before the opening is kept in one fixed array of device
+ * memory inside the library, GMM_NOALLOC_MAX_MASK_WORDS words (1 MiB), that
+ * every GPU loading the library holds until the process exits. Frames with
+ * H*ceil(W/32) above that limit (more than 8,388,608 pixels, e.g. 4096 x
+ * 2048) are rejected with GMM_EINVAL. All calls share the array: calls that
+ * can overlap on the GPU (different streams, or other threads) race on it
+ * and must be serialised by the caller. The first call on a device looks up
+ * the array's device address; make that first call before any stream
+ * capture. */
+#define GMM_NOALLOC_MAX_MASK_WORDS (1 << 18)
+int gmm_apply_open3_noalloc(const gmm_config *cfg, void *state, int first,
+                            const uint8_t *rgb8, const uint16_t *depth16,
+                            uint32_t *mask_out, void *stream);
+
 /* ------------------------------------------------------ multi-camera pool */
 /* Many cameras (the paper's future work, §VI: several RGB-D sensors), each
  * with its own resident model, advanced together: one persistent kernel

@@ -81,6 +81,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_state_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
         "gmm_fuse_masks": (ctypes.c_int, [_vp] * 4 + [ctypes.c_int, ctypes.c_int, _vp]),
         "gmm_morph_open3": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp]),
+        "gmm_apply_open3_noalloc": (ctypes.c_int, [ctypes.POINTER(GMMConfig), _vp, ctypes.c_int,
+                                                   _vp, _vp, _vp, _vp]),
         "gmm_pool_create": (_vp, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
         "gmm_pool_admit": (ctypes.c_int, [_vp, ctypes.POINTER(GMMConfig)]),
         "gmm_pool_release": (ctypes.c_int, [_vp, ctypes.c_int]),

@@ -1,0 +1,80 @@
+"""The allocation-free entry point gmm_apply_open3_noalloc, called through the
+C ABI, against the regular path (a handle created with morph_open = 1, whose
+gmm_apply keeps the unopened mask in a buffer it allocated).
+
+The allocation-free call exists for callers that must not allocate device
+memory (an application that reserves the GPU's memory up front, a real-time
+loop that may not wait on the allocator, code where allocation calls are not
+allowed): it keeps the unopened mask in a fixed array inside the library and
+takes the model state from the caller. Both paths run the same kernels, so
+the masks and the state must agree exactly, on two calls in a row (the first
+initialises the caller's state, the second updates it).
+
+This file is collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_2110_14934_gb300 as G
+from parity import scene_frames, to_dev, words
+
+pytestmark = pytest.mark.gpu
+
+
+def _config(L, H, W, M, prec):
+    cfg = G.GMMConfig()
+    L.gmm_config_init(ctypes.byref(cfg), H, W, M, 0.01, 2.5, 0.7, 225.0, 0.05)
+    cfg.precision = prec
+    return cfg
+
+
+def _caller_plane(state, H, W, M, prec, comp, field):
+    """Decode one plane of the caller-owned state (layout of gmm.h)."""
+    import torch
+    w_pad = ((W + 31) // 32) * 32
+    S = ((H * w_pad + 127) // 128) * 128
+    if prec == G.PREC_F32:
+        flat = state.view(torch.float32)
+    elif field in (G.PLANE_W_C, G.PLANE_W_D):
+        flat = state.view(torch.bfloat16)
+    else:
+        flat = state.view(torch.float16)
+    k = 8 * comp + field
+    return flat[k * S:k * S + H * w_pad].float().reshape(H, w_pad)[:, :W].cpu().numpy()
+
+
+@pytest.mark.parametrize("H,W,M,prec", [(45, 83, 3, G.PREC_F32), (120, 160, 5, G.PREC_F32),
+                                        (64, 96, 4, G.PREC_F16), (1, 1, 3, G.PREC_F32)])
+def test_noalloc_matches_handle_path_two_calls(H, W, M, prec):
+    import torch
+    L = G.load_library()
+    rgb, depth, _ = scene_frames(77 + M + H, H, W, 1, 48, 2)
+    ref = G.GMM(H, W, M, precision=prec, morph_open=True)
+    cfg = _config(L, H, W, M, prec)
+    # caller-owned state, deliberately not cleared: the first call initialises it
+    state = torch.full((G.state_bytes(H, W, M, prec),), 0xAB, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for t in range(2):
+        r, d = to_dev(rgb[t], depth[t])
+        want = ref.apply(r, d)
+        got = torch.full_like(want, -1)
+        rc = L.gmm_apply_open3_noalloc(ctypes.byref(cfg), state.data_ptr(), 1 if t == 0 else 0,
+                                       r.data_ptr(), d.data_ptr(), got.data_ptr(),
+                                       stream.cuda_stream)
+        assert rc == G.OK, L.gmm_last_error()
+        torch.cuda.synchronize()
+        assert np.array_equal(words(got), words(want)), f"mask differs on call {t}"
+        for comp in range(M):
+            for field in range(8):
+                a = _caller_plane(state, H, W, M, prec, comp, field)
+                b = ref.state_get(field, comp)
+                assert np.array_equal(a, b), (t, comp, G.PLANES[field])
+
+
+def test_noalloc_rejects_frames_above_the_scratch_limit():
+    L = G.load_library()
+    cfg = _config(L, 4096, 4097, 3, G.PREC_F32)  # 4096 * 129 words > 2^18
+    rc = L.gmm_apply_open3_noalloc(ctypes.byref(cfg), None, 1, None, None, None, None)
+    assert rc == G.EINVAL
+    assert "GMM_NOALLOC_MAX_MASK_WORDS" in L.gmm_last_error().decode()

@@ -41,13 +41,14 @@ WORKLOADS = {
     "c1": dict(name="single camera 1920x1080, M=5, FP32 state, 300-frame sequence",
                H=1080, W=1920, M=5, kind=1, frames=300, prec=0),
 }
+KERNELS = {"staged": 0, "direct": 1}
 METRIC = "Mpixel-frames/s (RGB+depth GMM+fusion)"
 UNIT = "Mpixel-frames/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129 * 1024 * 1024
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gmm_tick_f32_m5_1920x1080.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2110_14934_gb300", "csrc", f)
-                  for f in ("gmm_device.cuh", "gmm_kernels.cu")]
+                  for f in ("gmm_device.cuh", "gmm_kernels.cu", "gmm_staged.cu", "gmm_tma.cuh")]
 
 
 def bytes_per_pixel(M: int, prec: int) -> float:
@@ -289,6 +290,7 @@ def run_gmm(args, wl):
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
     g = G.GMM(H, W, M, precision=prec, device=dev, **PARAMS)
+    g.set_kernel(KERNELS[args.kernel], args.variant, args.ctas)
     mask = g.new_mask()
     K, Wm = args.steps, args.warmup
 
@@ -340,7 +342,8 @@ def run_gmm(args, wl):
 
     # end to end through the host-memory C-ABI path (pipelined, Fig. 4(a))
     e2e = run_e2e(G, torch, g_args=(H, W, M, prec), frames=(rgb_d, dep_d), dev=dev,
-                  steps=args.e2e_steps or K, warmup=Wm, world=world)
+                  steps=args.e2e_steps or K, warmup=Wm, world=world,
+                  kernel=(KERNELS[args.kernel], args.variant, args.ctas))
     del rgb_d, dep_d
     cpu = None
     if rank == 0 and world == 1 and args.cpu_frames > 0:
@@ -360,7 +363,9 @@ def run_gmm(args, wl):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src, "algorithmic_bytes_per_px": bpp,
-                         "kernel": f"k_tick<M={M},{'f32' if prec == 0 else 'f16'}>"},
+                         "kernel": (f"k_tick_staged<M={M},{'f32' if prec == 0 else 'f16'}>"
+                                    f" variant {args.variant}" if args.kernel == "staged" else
+                                    f"k_tick<M={M},{'f32' if prec == 0 else 'f16'}>")},
             "latency_ms": {"tick_p50": pct(tick_sorted, 50), "tick_p99": pct(tick_sorted, 99),
                            "e2e_p50": e2e["lat_p50"], "e2e_p99": e2e["lat_p99"]},
             "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
@@ -384,7 +389,7 @@ def pct(sorted_vals, p):
     return sorted_vals[i]
 
 
-def run_e2e(G, torch, g_args, frames, dev, steps, warmup, world):
+def run_e2e(G, torch, g_args, frames, dev, steps, warmup, world, kernel):
     """Host frames (pinned) -> C-ABI pipelined path -> host masks. Timed from
     the first submit to the last mask in host memory; per-frame latency from a
     separate unpipelined pass (submit, wait)."""
@@ -398,6 +403,7 @@ def run_e2e(G, torch, g_args, frames, dev, steps, warmup, world):
     ring = 8
     masks = torch.empty((ring, H, G.mask_words_per_row(W)), dtype=torch.int32).pin_memory()
     g = G.GMM(H, W, M, precision=prec, device=dev, **PARAMS)
+    g.set_kernel(*kernel)
     g.set_stream(torch.cuda.current_stream(dev))
     pending = []
 
@@ -439,6 +445,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gmm", "reference"], default="gmm")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c1")
     ap.add_argument("--e2e-steps", type=int, default=0, help="0: same as --steps")
+    ap.add_argument("--kernel", choices=sorted(KERNELS), default="direct")
+    ap.add_argument("--variant", type=int, default=0, help="staged tile shape 0-3")
+    ap.add_argument("--ctas", type=int, default=0, help="staged CTAs per SM (0: as many as fit)")
     ap.add_argument("--frames", type=int, default=0,
                     help="resident frames to cycle through (0: the workload's sequence length)")
     ap.add_argument("--cpu-frames", type=int, default=21, help="oracle baseline frames (0 = skip)")

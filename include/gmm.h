@@ -120,6 +120,19 @@ gmm_t *gmm_create_ex(const gmm_config *cfg);
  * default stream). The caller keeps the stream alive. */
 int gmm_set_stream(gmm_t *h, void *cuda_stream);
 
+/* Tick kernel of the handle (§IV: the per-pixel GPU pass). Both compute the
+ * same arithmetic bit for bit. GMM_KERNEL_DIRECT (default): one thread per
+ * pixel, coalesced loads and stores straight from and to HBM (always used
+ * for the initialising tick). GMM_KERNEL_STAGED: persistent CTAs stream
+ * tiles of the state through shared memory with bulk copies in a
+ * multi-stage pipeline; variant picks the tile shape (0: 256 pixels x 2
+ * stages, 1: 256 x 3, 2: 128 x 3, 3: 128 x 4), ctas_per_sm the residency
+ * (0 = as many as fit). A staged pipeline wait that runs out is reported by
+ * gmm_sync as GMM_ETIMEOUT. */
+#define GMM_KERNEL_STAGED 0
+#define GMM_KERNEL_DIRECT 1
+int gmm_set_kernel(gmm_t *h, int kind, int variant, int ctas_per_sm);
+
 /* One tick (§III.A-C, §IV): both mixtures and the List-1 fusion for one
  * RGB-D frame, in one fused kernel. rgb8, depth16: device, read-only.
  * mask_out: device, receives the fused foreground (bit-packed, see top), or

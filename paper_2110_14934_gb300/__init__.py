@@ -26,6 +26,7 @@ PLANE_W_C, PLANE_MU_R, PLANE_MU_G, PLANE_MU_B, PLANE_V_C, PLANE_W_D, PLANE_MU_D,
 PLANES = ("w_c", "mu_r", "mu_g", "mu_b", "v_c", "w_d", "mu_d", "v_d")
 PREC_F32, PREC_F16 = 0, 1
 PIPE_DEPTH = 3
+KERNEL_STAGED, KERNEL_DIRECT = 0, 1
 
 _ERRNAMES = {EINVAL: "GMM_EINVAL", ENOMEM: "GMM_ENOMEM", ECUDA: "GMM_ECUDA",
              EBUDGET: "GMM_EBUDGET", ETIMEOUT: "GMM_ETIMEOUT"}
@@ -66,6 +67,7 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_create": (_vp, [ctypes.c_int] * 3 + [ctypes.c_float] * 5),
         "gmm_create_ex": (_vp, [ctypes.POINTER(GMMConfig)]),
         "gmm_set_stream": (ctypes.c_int, [_vp, _vp]),
+        "gmm_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "gmm_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         "gmm_apply_ex": (ctypes.c_int, [_vp] * 6),
         "gmm_apply_host": (ctypes.c_int, [_vp] * 4),
@@ -225,6 +227,9 @@ class GMM:
 
     def set_stream(self, stream) -> None:
         _check(load_library().gmm_set_stream(self._h, _stream_ptr(stream, self.device)))
+
+    def set_kernel(self, kind: int = KERNEL_DIRECT, variant: int = 0, ctas_per_sm: int = 0) -> None:
+        _check(load_library().gmm_set_kernel(self._h, kind, variant, ctas_per_sm))
 
     # -- state -----------------------------------------------------------------
     def state_get(self, plane: int, component: int = 0) -> np.ndarray:

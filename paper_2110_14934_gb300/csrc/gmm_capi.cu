@@ -123,6 +123,13 @@ CamView make_view(const gmm_config &c, const Layout &L, void *arena, const uint8
     v.M = c.M;
     v.prec = c.precision;
     v.first = first;
+    if (L.wpr > 1) {
+        uint32_t l = 0;
+        while ((1u << l) < (uint32_t)L.wpr)
+            ++l; // l = ceil(log2(wpr)) >= 1
+        v.wpr_mul = (uint32_t)(((1ull << (31 + l)) + (uint64_t)L.wpr - 1) / (uint64_t)L.wpr);
+        v.wpr_shift = l - 1;
+    }
     v.pc = stream_prm(c, false);
     v.pd = stream_prm(c, true);
     return v;
@@ -307,6 +314,9 @@ struct gmm_ctx {
     long long slot_ticket[GMM_PIPE_DEPTH] = {-1, -1, -1};
     long long next_ticket = 0;
     long long done_upto = -1;
+    // tick kernel selection and the staged kernel's wait-status word
+    int kernel = GMM_KERNEL_DIRECT, variant = 0, ctas_per_sm = 0;
+    int *d_status = nullptr;
 };
 
 static int launch_apply(gmm_ctx *h, const uint8_t *rgb, const uint16_t *depth, uint32_t *mask,
@@ -314,7 +324,11 @@ static int launch_apply(gmm_ctx *h, const uint8_t *rgb, const uint16_t *depth, u
     uint32_t *tick_mask = h->cfg.morph_open ? h->morph_tmp : mask;
     CamView v = make_view(h->cfg, h->L, h->arena, rgb, depth, tick_mask, fgr, fgd,
                           h->initialized ? 0 : 1);
-    cudaError_t e = gmmhost::launch_tick(v, 256, h->stream);
+    cudaError_t e;
+    if (h->initialized && h->kernel == GMM_KERNEL_STAGED)
+        e = gmmhost::launch_tick_staged(v, h->variant, h->ctas_per_sm, h->d_status, h->stream);
+    else
+        e = gmmhost::launch_tick(v, 256, h->stream);
     if (e == cudaSuccess && h->cfg.morph_open)
         e = gmmhost::launch_morph_open3(h->morph_tmp, mask, h->cfg.H, h->cfg.W, h->stream);
     if (e != cudaSuccess)
@@ -375,6 +389,10 @@ gmm_t *gmm_create_ex(const gmm_config *cfg) {
         e = cudaMemset(h->arena, 0, h->L.total);
     if (e == cudaSuccess && cfg->morph_open)
         e = cudaMalloc(&h->morph_tmp, (size_t)cfg->H * h->L.wpr * 4);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&h->d_status, 256);
+    if (e == cudaSuccess)
+        e = cudaMemset(h->d_status, 0, 256);
     if (e != cudaSuccess) {
         const bool oom = e == cudaErrorMemoryAllocation;
         if (oom)
@@ -386,6 +404,8 @@ gmm_t *gmm_create_ex(const gmm_config *cfg) {
             cudaFree(h->arena);
         if (h->morph_tmp)
             cudaFree(h->morph_tmp);
+        if (h->d_status)
+            cudaFree(h->d_status);
         delete h;
         return nullptr;
     }
@@ -563,10 +583,30 @@ int gmm_sync(gmm_t *h) {
     if (!h)
         return fail(GMM_EINVAL, "gmm_sync: null handle");
     DeviceGuard g(h->device);
-    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    int status = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess)
         return cuda_fail(&h->sticky, e, "gmm_sync");
+    if (status != 0)
+        return fail(GMM_ETIMEOUT, "gmm_sync: a staged-kernel pipeline wait ran out");
     return h->sticky == cudaSuccess ? GMM_OK : fail(GMM_ECUDA, "gmm_sync: earlier CUDA failure");
+}
+
+int gmm_set_kernel(gmm_t *h, int kind, int variant, int ctas_per_sm) {
+    if (!h)
+        return fail(GMM_EINVAL, "gmm_set_kernel: null handle");
+    if (kind != GMM_KERNEL_STAGED && kind != GMM_KERNEL_DIRECT)
+        return fail(GMM_EINVAL, "gmm_set_kernel: unknown kernel kind");
+    if (variant < 0 || variant > 3)
+        return fail(GMM_EINVAL, "gmm_set_kernel: variant must be in [0, 3]");
+    if (ctas_per_sm < 0 || ctas_per_sm > 32)
+        return fail(GMM_EINVAL, "gmm_set_kernel: ctas_per_sm must be in [0, 32]");
+    h->kernel = kind;
+    h->variant = variant;
+    h->ctas_per_sm = ctas_per_sm;
+    return GMM_OK;
 }
 
 int gmm_destroy(gmm_t *h) {
@@ -591,6 +631,8 @@ int gmm_destroy(gmm_t *h) {
     cudaFree(h->arena);
     if (h->morph_tmp)
         cudaFree(h->morph_tmp);
+    if (h->d_status)
+        cudaFree(h->d_status);
     delete h;
     return GMM_OK;
 }

@@ -37,11 +37,21 @@ struct CamView {
     uint32_t *fg_rgb;      // optional colour foreground words (may be null)
     uint32_t *fg_d;        // optional depth foreground words (may be null)
     int64_t stride;        // plane stride in elements
-    int64_t n_pad;         // H*w_pad
+    int64_t n_pad;         // H*w_pad (< 2^30)
     int H, W, w_pad, wpr;  // wpr = words per mask row = w_pad / 32
     int M, prec, first, pad;
+    uint32_t wpr_mul, wpr_shift; // n / wpr == umulhi(n, wpr_mul) >> wpr_shift (wpr > 1)
     StreamPrm pc, pd;
 };
+
+// Row of mask word n (n < 2^31): division by the words-per-row constant as a
+// multiply-high and shift. With l = ceil(log2 d) and m = ceil(2^(31+l) / d),
+// m < 2^32 and floor(n m / 2^(31+l)) = floor(n / d) for every n < 2^31
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994).
+__device__ __forceinline__ uint32_t div_wpr(uint32_t n, const CamView &cv) {
+    return cv.wpr == 1 ? n : (__umulhi(n, cv.wpr_mul) >> cv.wpr_shift);
+}
 
 // ------------------------------------------------------------ storage types
 template <int PREC> struct Storage;
@@ -221,11 +231,12 @@ __device__ __forceinline__ uint32_t fuse_list1(int fgc, int fgd, uint32_t fb) {
 template <int M, int PREC>
 __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) {
     using S = Storage<PREC>;
-    const int64_t row = (p >> 5) / cv.wpr;
-    const int x = (int)(p - row * cv.w_pad);
-    if (x >= cv.W)
+    const uint32_t p32 = (uint32_t)p;
+    const uint32_t row = div_wpr(p32 >> 5, cv);
+    const uint32_t x = p32 - row * (uint32_t)cv.w_pad;
+    if (x >= (uint32_t)cv.W)
         return 0u;
-    const int64_t q = row * cv.W + x;
+    const int64_t q = (int64_t)row * cv.W + x;
     const float xc[3] = {(float)cv.rgb[3 * q], (float)cv.rgb[3 * q + 1],
                          (float)cv.rgb[3 * q + 2]};
     const uint32_t draw = cv.depth[q];

@@ -11,6 +11,13 @@ namespace gmmhost {
 // Single-camera tick: one thread per padded pixel. threads: block size.
 cudaError_t launch_tick(const gmmdev::CamView &cv, int threads, cudaStream_t s);
 
+// Staged single-camera tick (bulk-copy pipeline through shared memory).
+// variant: tile shape (0: 256 px x 2 stages, 1: 256 x 3, 2: 128 x 3,
+// 3: 128 x 4); ctas_per_sm: 0 = as many as fit. status: device word that
+// gets bit 0 set if a pipeline wait runs out. Not for first ticks.
+cudaError_t launch_tick_staged(const gmmdev::CamView &cv, int variant, int ctas_per_sm,
+                               int *status, cudaStream_t s);
+
 // List 1 alone over bit-packed inputs.
 cudaError_t launch_fuse(const uint32_t *fg_rgb, const uint32_t *fg_d, uint8_t *fusion,
                         uint32_t *mask, int H, int W, cudaStream_t s);

@@ -35,11 +35,13 @@ def words(t) -> np.ndarray:
 class Pair:
     """A GPU model and an oracle model with the same parameters."""
 
-    def __init__(self, H, W, M, precision=G.PREC_F32, eps=1e-5, **kw):
+    def __init__(self, H, W, M, precision=G.PREC_F32, eps=1e-5, kernel=G.KERNEL_DIRECT,
+                 variant=0, **kw):
         p = dict(DEFAULTS)
         p.update(kw)
         self.H, self.W, self.M = H, W, M
         self.gpu = G.GMM(H, W, M, precision=precision, **p)
+        self.gpu.set_kernel(kernel, variant)
         self.orc = O.OracleGMM(H, W, M, p["alpha"], p["match_k"], p["bg_T"], p["init_var"],
                                p["init_w"], init_var_d=p.get("init_var_d"),
                                v_min_c=p.get("v_min_c", 1.0), v_min_d=p.get("v_min_d", 1.0),

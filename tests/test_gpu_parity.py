@@ -32,14 +32,18 @@ def _assert_tick(pair, g, o, label):
     return int(np.count_nonzero(exempt))
 
 
+KERNELS = [pytest.param(G.KERNEL_STAGED, id="staged"), pytest.param(G.KERNEL_DIRECT, id="direct")]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("M", [3, 4, 5])
 @pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("H,W", [(45, 83), (64, 96)])
-def test_single_step_parity(M, kind, H, W):
+def test_single_step_parity(M, kind, H, W, kernel):
     """Oracle state after 44 frames loaded into the GPU, then ten teacher-forced
     ticks across the illumination step at frame 50."""
     rgb, depth, _ = scene_frames(100 + M, H, W, kind, 0, 55)
-    pair = Pair(H, W, M)
+    pair = Pair(H, W, M, kernel=kernel)
     for t in range(45):
         pair.orc.tick(rgb[t], depth[t])
     pair.load_gpu_from_oracle()
@@ -152,11 +156,12 @@ def pair_tick_gpu_only(pair, rgb, depth):
             "fg_d": G.unpack_mask(words(fd), pair.H, pair.W)}, None
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("H,W,M", [(1, 1, 3), (1, 33, 5), (33, 1, 4), (2, 31, 3), (3, 64, 5),
                                    (7, 95, 4)])
-def test_edge_shapes_teacher_forced(H, W, M):
+def test_edge_shapes_teacher_forced(H, W, M, kernel):
     rgb, depth, _ = scene_frames(31 + H * W, H, W, 1, 40, 25)
-    pair = Pair(H, W, M)
+    pair = Pair(H, W, M, kernel=kernel)
     for t in range(25):
         g, o = pair.tick(rgb[t], depth[t])
         _assert_tick(pair, g, o, f"{H}x{W} frame {t}")
@@ -223,14 +228,15 @@ def test_reset_reinitialises():
     assert sum(st["bad"]) == 0, st
 
 
-def test_fp16_state_single_step():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp16_state_single_step(kernel):
     """FP16 means/variances, BF16 weights, FP32 arithmetic: one tick from a
     state rounded to the storage types, against the oracle from the same
     rounded state; the tolerance is the storage rounding (half an ulp of
     float16 / bfloat16)."""
     H, W, M = 48, 96, 5
     rgb, depth, _ = scene_frames(12, H, W, 1, 0, 50)
-    pair = Pair(H, W, M, precision=G.PREC_F16)
+    pair = Pair(H, W, M, precision=G.PREC_F16, kernel=kernel)
     for t in range(40):
         pair.orc.tick(rgb[t], depth[t])
     pair.load_gpu_from_oracle()
@@ -248,3 +254,35 @@ def test_fp16_state_single_step():
             st = state_mismatch(gp, op, fus, exclude=exempt, rtol=tol * 1.01, floors=floors)
             assert st["bad"][f] == 0, (t, f, st)
         pair.sync_oracle_to_gpu()
+
+
+@pytest.mark.parametrize("prec", [G.PREC_F32, G.PREC_F16])
+@pytest.mark.parametrize("H,W,M", [(120, 160, 5), (45, 83, 3), (37, 1000, 4), (1, 1, 5)])
+def test_staged_variants_match_direct(H, W, M, prec):
+    """Every staged tile shape computes exactly what the direct kernel does
+    (same arithmetic, different data movement): masks and state bit-equal
+    over ticks that cross the illumination step, with ragged last tiles."""
+    import torch
+    rgb, depth, _ = scene_frames(900 + M, H, W, 1, 44, 9)
+    ref = G.GMM(H, W, M, precision=prec)
+    ref.set_kernel(G.KERNEL_DIRECT)
+    staged = []
+    for variant in range(4):
+        g = G.GMM(H, W, M, precision=prec)
+        g.set_kernel(G.KERNEL_STAGED, variant)
+        staged.append(g)
+    for t in range(9):
+        r, d = to_dev(rgb[t], depth[t])
+        outs = []
+        for g in [ref] + staged:
+            m = g.new_mask(); fc = g.new_mask(); fd = g.new_mask()
+            g.apply(r, d, m, fc, fd)
+            outs.append((m, fc, fd))
+        torch.cuda.synchronize()
+        for v, o in enumerate(outs[1:]):
+            for a, b in zip(outs[0], o):
+                assert torch.equal(a, b), (t, v)
+    for v, g in enumerate(staged):
+        assert np.array_equal(g.planes(), ref.planes()), v
+        assert np.array_equal(g.fusion(), ref.fusion()), v
+        g.sync()  # also reports a pipeline wait that ran out

@@ -40,7 +40,15 @@ WORKLOADS = {
                H=480, W=640, M=3, kind=0, frames=100, prec=0),
     "c1": dict(name="single camera 1920x1080, M=5, FP32 state, 300-frame sequence",
                H=1080, W=1920, M=5, kind=1, frames=300, prec=0),
+    "c2": dict(name="64 cameras (16 each at 320x240, 640x480, 1280x720, 1920x1080), M from "
+                    "{3,5} by seed, FP32 state, 300-frame sequences, one persistent launch per "
+                    "tick (CUDA graph, autotuned launch shape)",
+               pool=True, cams_per_res=16, frames=300, prec=0, M=5),
+    "c3": dict(name="the 64-camera mix of c2 with FP16 means/variances and BF16 weights (FP32 "
+                    "arithmetic), 1000 ticks over 300 resident frames per camera",
+               pool=True, cams_per_res=16, frames=300, prec=1, M=5),
 }
+CAMERA_RESOLUTIONS = [(240, 320), (480, 640), (720, 1280), (1080, 1920)]
 KERNELS = {"staged": 0, "direct": 1}
 METRIC = "Mpixel-frames/s (RGB+depth GMM+fusion)"
 UNIT = "Mpixel-frames/s"
@@ -222,37 +230,54 @@ def oracle_rate(wl: dict, frames: int, rows: int, seed: int):
                               f"({rows}x{W} px per frame), FP64, 1 thread"
 
 
+def reference_cameras(wl):
+    """(H, W, M, seed, scene kind) the reference arm samples: the workload's
+    camera, or one camera per resolution of a many-camera mix."""
+    if wl.get("pool"):
+        mix = camera_mix(wl["cams_per_res"], 0)
+        return [(H, W, M, seed, 1) for (H, W, M, seed) in mix[::wl["cams_per_res"]]]
+    return [(wl["H"], wl["W"], wl["M"], 1, wl["kind"])]
+
+
 def run_reference(args, wl):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    # size each step's sample so that warmup + steps take about a minute
-    probe_rate, _, _ = oracle_rate(wl, 3, 16, 1)
-    target_s = float(os.environ.get("GMM_REFERENCE_SECONDS", "60"))
-    steps = args.steps + args.warmup
-    rows = int(max(1, min(wl["H"], target_s * probe_rate * 1e6 / max(steps, 1) / wl["W"])))
     import oracle as O
     import synth
-    H, W, M = wl["H"], wl["W"], wl["M"]
-    y0 = (H - rows) // 2
-    s = synth.scene(1, H, W, wl["kind"])
-    nf = min(wl["frames"], steps + 1)
-    rgb, dep, _ = synth.rows_host(s, 0, nf, y0, rows)
-    g = O.OracleGMM(rows, W, M, **PARAMS)
+    cams = reference_cameras(wl)
+    steps = args.steps + args.warmup
+    # size each step's sample so that warmup + steps take about a minute
+    H0, W0, M0, s0, k0 = max(cams, key=lambda c: c[0] * c[1])
+    probe_rate, _, _ = oracle_rate(dict(H=H0, W=W0, M=M0, kind=k0), 3, 16, s0)
+    target_s = float(os.environ.get("GMM_REFERENCE_SECONDS", "60"))
+    px_per_cam = target_s * probe_rate * 1e6 / max(steps, 1) / len(cams)
+    bands, descr = [], []
+    for (H, W, M, seed, kind) in cams:
+        rows = int(max(1, min(H, px_per_cam / W)))
+        y0 = (H - rows) // 2
+        nf = min(wl["frames"], steps + 1)
+        rgb, dep, _ = synth.rows_host(synth.scene(seed, H, W, kind), 0, nf, y0, rows)
+        bands.append((O.OracleGMM(rows, W, M, **PARAMS), rgb, dep, nf, rows * W))
+        descr.append(f"rows {y0}-{y0 + rows - 1} of a {W}x{H} M={M} camera")
     for k in range(args.warmup):
-        g.tick(rgb[k % nf], dep[k % nf])
+        for g, rgb, dep, nf, _ in bands:
+            g.tick(rgb[k % nf], dep[k % nf])
     t = time.perf_counter()
     for k in range(args.steps):
-        f = (args.warmup + k) % nf
-        g.tick(rgb[f], dep[f])
+        for g, rgb, dep, nf, _ in bands:
+            f = (args.warmup + k) % nf
+            g.tick(rgb[f], dep[f])
     dt = time.perf_counter() - t
-    value = args.steps * rows * W / dt / 1e6
-    sample = f"each step: rows {y0}-{y0 + rows - 1} ({rows}x{W} px) of one frame, FP64, 1 thread"
+    value = args.steps * sum(b[4] for b in bands) / dt / 1e6
+    sample = "each step: " + "; ".join(descr) + " (one frame each), FP64, 1 thread"
+    cfg = (pool_config(args.workload, wl, world, camera_mix(wl["cams_per_res"], 0), None, None)
+           if wl.get("pool") else config_dict(args.workload, wl, world))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_dict(args.workload, wl, world),
+        "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -382,6 +407,243 @@ def run_gmm(args, wl):
     return 0
 
 
+# ---------------------------------------------------------------- many cameras
+def camera_mix(cams_per_res: int, rank: int):
+    """(H, W, M, seed) of every camera of a rank: cams_per_res cameras at each
+    resolution, each with its own seed; M drawn from {3, 5} by the seed."""
+    import random
+    out = []
+    for ri, (H, W) in enumerate(CAMERA_RESOLUTIONS):
+        for i in range(cams_per_res):
+            seed = rank_seed(1000 + 100 * ri + i, rank)
+            out.append((H, W, random.Random(seed).choice((3, 5)), seed))
+    return out
+
+
+def pool_config(key, wl, world, cams, shape, graph):
+    px = sum(H * W for (H, W, _, _) in cams)
+    state = sum(H * W * M * (32 if wl["prec"] == 0 else 16) for (H, W, M, _) in cams)
+    return {"workload": f"{key}: {wl['name']}", "cameras_per_gpu": len(cams),
+            "pixels_per_tick": px, "M3_cameras": sum(1 for c in cams if c[2] == 3),
+            "M5_cameras": sum(1 for c in cams if c[2] == 5),
+            "state": "f32" if wl["prec"] == 0 else "f16/bf16",
+            "alpha": PARAMS["alpha"], "k": PARAMS["match_k"], "T": PARAMS["bg_T"],
+            "launch": shape, "cuda_graph": graph, "parallelism": f"camera-sharded x{world}",
+            "l2": f"state {state / 1e9:.1f} GB per GPU vs L2 129 MB: inputs larger than L2 "
+                  "between iterations"}
+
+
+def run_pool(args, wl):
+    import torch
+    import paper_2110_14934_gb300 as G
+    import synth
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    prec = wl["prec"]
+    cams = camera_mix(wl["cams_per_res"], rank)
+    nf = min(wl["frames"], args.frames) if args.frames > 0 else wl["frames"]
+    K, Wm = args.steps, args.warmup
+    stream = torch.cuda.current_stream(dev)
+    frames = []
+    for (H, W, M, seed) in cams:
+        r, d, _ = synth.frames_device(synth.scene(seed, H, W, 1), 0, nf, device=dev, with_gt=False)
+        frames.append((r, d))
+    masks = [torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device=dev)
+             for (H, W, _, _) in cams]
+    torch.cuda.synchronize()
+    rgb_base = [f[0].data_ptr() for f in frames]
+    dep_base = [f[1].data_ptr() for f in frames]
+    rgb_step = [H * W * 3 for (H, W, _, _) in cams]
+    dep_step = [H * W * 2 for (H, W, _, _) in cams]
+    mask_ptr = [m.data_ptr() for m in masks]
+
+    pool = G.Pool(precision=prec, max_cams=len(cams), device=dev)
+    ids = [pool.admit(H, W, M, **PARAMS) for (H, W, M, _) in cams]
+    pool.set_stream(stream)
+    graph = not args.no_graph
+    pool.use_graph(graph)
+
+    def submit(f):
+        pool.submit_many(ids, [b + f * s for b, s in zip(rgb_base, rgb_step)],
+                         [b + f * s for b, s in zip(dep_base, dep_step)], mask_ptr)
+
+    submit(0)
+    shape = pool.autotune(iters=3) if not args.no_autotune else None
+    pool.tick(stream)  # frame 0 initialises every model
+    for k in range(1, Wm):
+        submit(k % nf)
+        pool.tick(stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.wait_first()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world, dev)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    t0.record(stream)
+    for k in range(K):
+        submit((Wm + k) % nf)
+        pool.tick(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world, dev)
+    if clocks:
+        clocks.stop()
+    local_ms = t0.elapsed_time(t1)
+    total_ms = reduce_max(local_ms, world, dev)
+    px = sum(H * W for (H, W, _, _) in cams)
+    value = aggregate_mpx_per_s(world, K, px, total_ms)
+    tick_bytes = sum(H * W * bytes_per_pixel(M, prec) for (H, W, M, _) in cams)
+    achieved = tick_bytes / (local_ms / K / 1e3) / 1e9
+    peak, peak_src = measured_hbm_peak()
+
+    # per-tick device latency
+    n_lat = min(K, 500)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(n_lat)]
+    for k in range(n_lat):
+        submit((Wm + K + k) % nf)
+        ev[k][0].record(stream)
+        pool.tick(stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    tick_ms = sorted(a.elapsed_time(b) for a, b in ev)
+
+    # The plain path: one FP32 handle per camera, one launch per camera per tick.
+    L = G.load_library()
+    plain = [G.GMM(H, W, M, precision=G.PREC_F32, device=dev, **PARAMS) for (H, W, M, _) in cams]
+    for g in plain:
+        g.set_stream(stream)
+    hs = [g._h for g in plain]
+    n_plain = min(K, 300)
+    for k in range(Wm):
+        for i, h in enumerate(hs):
+            L.gmm_apply(h, rgb_base[i] + (k % nf) * rgb_step[i], dep_base[i] + (k % nf) * dep_step[i],
+                        mask_ptr[i])
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for k in range(n_plain):
+        f = (Wm + k) % nf
+        for i, h in enumerate(hs):
+            L.gmm_apply(h, rgb_base[i] + f * rgb_step[i], dep_base[i] + f * dep_step[i], mask_ptr[i])
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = reduce_max(p0.elapsed_time(p1), world, dev)
+    plain_value = aggregate_mpx_per_s(world, n_plain, px, plain_ms)
+    for g in plain:
+        g.close()
+
+    e2e = run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, args.e2e_steps or min(K, 600),
+                       Wm, world)
+    clk = None
+    if clocks:
+        clk = clocks.summary()
+        clocks.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": pool_config(args.workload, wl, world, cams, shape, graph),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "algorithmic_bytes_per_tick": tick_bytes,
+                         "kernel": f"k_pool_tick<{'f32' if prec == 0 else 'f16'}>"},
+            "plain_one_camera_per_launch_f32": {"value": plain_value, "unit": UNIT,
+                                                "steps": n_plain,
+                                                "pooled_over_plain": value / plain_value},
+            "latency_ms": {"tick_p50": pct(tick_ms, 50), "tick_p99": pct(tick_ms, 99)},
+            "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
+                    "d2h_bytes_per_step": e2e["d2h"],
+                    "path": "pinned packed tick-sets -> device staging (copy stream) -> "
+                            "gmm_pool_submit_many + gmm_pool_tick -> masks to pinned host"},
+            "cpu_baseline": None,
+            "gpu_launches": K,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    pool.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, steps, warmup, world):
+    """Frames from pinned host memory each tick: every camera's frame of a
+    tick is packed into one pinned buffer, uploaded with one copy into one of
+    two device staging buffers on a copy stream (overlapping the previous
+    tick's compute), the pool ticks from there, and the packed masks come back
+    with one copy on a third stream."""
+    def al(x):
+        return (x + 255) // 256 * 256
+    off, o = [], 0
+    for (H, W, _, _) in cams:
+        off.append((o, o + al(H * W * 3)))
+        o += al(H * W * 3) + al(H * W * 2)
+    set_bytes = o
+    moff, mo = [], 0
+    for (H, W, _, _) in cams:
+        moff.append(mo)
+        mo += al(H * G.mask_words_per_row(W) * 4)
+    mask_bytes = mo
+    ring = 3
+    host = torch.empty((ring, set_bytes), dtype=torch.uint8).pin_memory()
+    for r in range(ring):
+        for (a, b), (rg, dp), (H, W, _, _) in zip(off, frames, cams):
+            host[r, a:a + H * W * 3].copy_(rg[r].reshape(-1))
+            host[r, b:b + H * W * 2].copy_(dp[r].reshape(-1).view(torch.uint8))
+    stage = torch.empty((2, set_bytes), dtype=torch.uint8, device=dev)
+    dmask = torch.empty((2, mask_bytes), dtype=torch.uint8, device=dev)
+    hmask = torch.empty((ring, mask_bytes), dtype=torch.uint8).pin_memory()
+    up_s, down_s = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    up = [torch.cuda.Event() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    down = [torch.cuda.Event() for _ in range(2)]
+
+    def tick(k):
+        b, r = k % 2, k % ring
+        with torch.cuda.stream(up_s):
+            up_s.wait_event(done[b])        # tick k-2 has finished reading stage b
+            stage[b].copy_(host[r], non_blocking=True)
+            up[b].record(up_s)
+        stream.wait_event(up[b])
+        stream.wait_event(down[b])          # tick k-2's masks have left dmask b
+        sb, mb = stage[b].data_ptr(), dmask[b].data_ptr()
+        pool.submit_many(ids, [sb + a for a, _ in off], [sb + c for _, c in off],
+                         [mb + m for m in moff])
+        pool.tick(stream)
+        done[b].record(stream)
+        with torch.cuda.stream(down_s):
+            down_s.wait_event(done[b])
+            hmask[k % ring].copy_(dmask[b], non_blocking=True)
+            down[b].record(down_s)
+
+    for k in range(warmup):
+        tick(k)
+    torch.cuda.synchronize()
+    barrier(world, dev)
+    t = time.perf_counter()
+    for k in range(steps):
+        tick(warmup + k)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    barrier(world, dev)
+    dt = reduce_max(dt, world, dev)
+    px = sum(H * W for (H, W, _, _) in cams)
+    return {"value": world * steps * px / dt / 1e6,
+            "h2d": sum(H * W * 5 for (H, W, _, _) in cams),
+            "d2h": sum(H * G.mask_words_per_row(W) * 4 for (H, W, _, _) in cams)}
+
+
 def pct(sorted_vals, p):
     if not sorted_vals:
         return None
@@ -448,6 +710,8 @@ def main(argv=None):
     ap.add_argument("--kernel", choices=sorted(KERNELS), default="direct")
     ap.add_argument("--variant", type=int, default=0, help="staged tile shape 0-3")
     ap.add_argument("--ctas", type=int, default=0, help="staged CTAs per SM (0: as many as fit)")
+    ap.add_argument("--no-graph", action="store_true", help="pooled workloads: no CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true", help="pooled workloads: default launch")
     ap.add_argument("--frames", type=int, default=0,
                     help="resident frames to cycle through (0: the workload's sequence length)")
     ap.add_argument("--cpu-frames", type=int, default=21, help="oracle baseline frames (0 = skip)")
@@ -458,6 +722,8 @@ def main(argv=None):
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
+    if wl.get("pool"):
+        return run_pool(args, wl)
     return run_gmm(args, wl)
 
 

@@ -125,9 +125,8 @@ int gmm_set_stream(gmm_t *h, void *cuda_stream);
  * pixel, coalesced loads and stores straight from and to HBM (always used
  * for the initialising tick). GMM_KERNEL_STAGED: persistent CTAs stream
  * tiles of the state through shared memory with bulk copies in a
- * multi-stage pipeline; variant picks the tile shape (0: 256 pixels x 2
- * stages, 1: 256 x 3, 2: 128 x 3, 3: 128 x 4), ctas_per_sm the residency
- * (0 = as many as fit). A staged pipeline wait that runs out is reported by
+ * multi-stage pipeline; variant picks the depth (0..3: 2..5 stages of one
+ * 256-pixel tile each), ctas_per_sm the residency (0 = as many as fit). A staged pipeline wait that runs out is reported by
  * gmm_sync as GMM_ETIMEOUT. */
 #define GMM_KERNEL_STAGED 0
 #define GMM_KERNEL_DIRECT 1
@@ -227,10 +226,12 @@ int gmm_morph_open3(const uint32_t *mask_in, uint32_t *mask_out, int H, int W,
  * cudaFree or any allocating routine.
  *
  * The caller provides the model state: `state` is device memory of
- * gmm_state_bytes(H, W, M, precision) bytes, 16-byte aligned, laid out as
- * M*8 planes (plane 8*i + GMM_PLANE_*, i the rank) of S elements each,
- * S = H*ceil(W/32)*32 rounded up to a multiple of 128, rows padded to a
- * multiple of 32 pixels, followed by the per-pixel List-1 bytes. The state
+ * gmm_state_bytes(H, W, M, precision) bytes, 16-byte aligned. Pixels are
+ * numbered p = y*Wp + x with Wp = ceil(W/32)*32 and grouped in tiles of 256:
+ * tile t holds M*8 planes of 256 elements (plane 8*i + GMM_PLANE_*, i the
+ * rank; float32, or bfloat16 weights and float16 means and variances), so
+ * element (plane k, pixel p) is at index ((p/256)*8*M + k)*256 + p%256;
+ * the ceil(H*Wp/256) tiles are followed by one List-1 byte per tiled pixel. The state
  * persists between calls; first = 1 initialises it from this frame (it
  * need not be cleared beforehand), first = 0 updates it. cfg gives the
  * model parameters (its morph_open field is ignored). rgb8, depth16 and
@@ -278,13 +279,21 @@ int gmm_pool_submit(gmm_pool_t *p, int cam, const uint8_t *rgb8,
                     const uint16_t *depth16, uint32_t *mask_out,
                     uint32_t *fg_rgb_out, uint32_t *fg_d_out);
 
+/* n submissions in one call: entry i is (cams[i], rgb8[i], depth16[i],
+ * mask_out[i]) as for gmm_pool_submit (no per-stream masks). Host arrays of
+ * n entries each; the pointers they hold are device pointers. Stops at the
+ * first bad entry and returns its status (earlier entries stay submitted). */
+int gmm_pool_submit_many(gmm_pool_t *p, int n, const int *cams,
+                         const uint8_t *const *rgb8, const uint16_t *const *depth16,
+                         uint32_t *const *mask_out);
+
 /* Advance every submitted camera by one frame in one launch (asynchronous
  * on the pool's stream), then clear the submissions. */
 int gmm_pool_tick(gmm_pool_t *p);
 
 int gmm_pool_set_stream(gmm_pool_t *p, void *cuda_stream);
 
-/* Launch shape of the persistent kernel: threads per block (64..512, a
+/* Launch shape of the persistent kernel: threads per block (64..256, a
  * multiple of 32), CTAs per SM (>= 1), pixels per tile (a multiple of the
  * block size). 0 keeps the current value. */
 int gmm_pool_set_launch(gmm_pool_t *p, int threads, int ctas_per_sm,

@@ -89,6 +89,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_pool_admit": (ctypes.c_int, [_vp, ctypes.POINTER(GMMConfig)]),
         "gmm_pool_release": (ctypes.c_int, [_vp, ctypes.c_int]),
         "gmm_pool_submit": (ctypes.c_int, [_vp, ctypes.c_int] + [_vp] * 5),
+        "gmm_pool_submit_many": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+                                 + [ctypes.POINTER(ctypes.c_void_p)] * 3),
         "gmm_pool_tick": (ctypes.c_int, [_vp]),
         "gmm_pool_set_stream": (ctypes.c_int, [_vp, _vp]),
         "gmm_pool_set_launch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -314,6 +316,15 @@ class Pool:
         _check_frame(rgb, depth, H, W)
         _check(load_library().gmm_pool_submit(self._p, cam, _ptr(rgb), _ptr(depth), _ptr(mask),
                                               _ptr(fg_rgb), _ptr(fg_d)))
+
+    def submit_many(self, cams, rgb_ptrs, depth_ptrs, mask_ptrs) -> None:
+        """Submit many cameras at once from raw device pointers (ints)."""
+        n = len(cams)
+        ca = (ctypes.c_int * n)(*cams)
+        ra = (ctypes.c_void_p * n)(*rgb_ptrs)
+        da = (ctypes.c_void_p * n)(*depth_ptrs)
+        ma = (ctypes.c_void_p * n)(*mask_ptrs)
+        _check(load_library().gmm_pool_submit_many(self._p, n, ca, ra, da, ma))
 
     def tick(self, stream=None) -> None:
         L = load_library()

@@ -51,9 +51,11 @@ Layout make_layout(int H, int W, int M, int prec) {
     L.wpr = L.w_pad / 32;
     L.n_pad = (int64_t)H * L.w_pad;
     L.elem = prec == GMM_PREC_F32 ? 4 : 2;
-    L.stride = ((L.n_pad + 127) / 128) * 128; // 256-byte aligned planes in both precisions
-    L.planes_bytes = (size_t)M * gmmdev::kFields * (size_t)L.stride * L.elem;
-    L.fusion_bytes = (size_t)((L.n_pad + 255) / 256) * 256;
+    L.n_tiles = (L.n_pad + gmmdev::kTile - 1) / gmmdev::kTile;
+    L.planes_per_tile = M * gmmdev::kFields;
+    L.tile_bytes = (size_t)L.planes_per_tile * gmmdev::kTile * L.elem;
+    L.planes_bytes = (size_t)L.n_tiles * L.tile_bytes;
+    L.fusion_bytes = (size_t)L.n_tiles * gmmdev::kTile;
     L.total = L.planes_bytes + L.fusion_bytes;
     return L;
 }
@@ -114,7 +116,7 @@ CamView make_view(const gmm_config &c, const Layout &L, void *arena, const uint8
     v.mask = mask;
     v.fg_rgb = fgr;
     v.fg_d = fgd;
-    v.stride = L.stride;
+    v.n_tiles = L.n_tiles;
     v.n_pad = L.n_pad;
     v.H = c.H;
     v.W = c.W;
@@ -223,9 +225,12 @@ int state_get_common(const gmm_config &c, const Layout &L, const void *arena,
     }
     const int pi = comp * gmmdev::kFields + plane;
     const bool weight = plane == GMM_PLANE_W_C || plane == GMM_PLANE_W_D;
-    std::vector<uint8_t> tmp((size_t)L.n_pad * L.elem);
-    const uint8_t *src = static_cast<const uint8_t *>(arena) + (size_t)pi * L.stride * L.elem;
-    cudaError_t e = cudaMemcpyAsync(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost, stream);
+    // One plane is a kTile-element run in every tile: a pitched copy.
+    const size_t run = (size_t)gmmdev::kTile * L.elem;
+    std::vector<uint8_t> tmp((size_t)L.n_tiles * run);
+    const uint8_t *src = static_cast<const uint8_t *>(arena) + (size_t)pi * run;
+    cudaError_t e = cudaMemcpy2DAsync(tmp.data(), run, src, L.tile_bytes, run, (size_t)L.n_tiles,
+                                      cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess)
@@ -260,10 +265,12 @@ int state_set_common(const gmm_config &c, const Layout &L, void *arena, cudaStre
     } else {
         const int pi = comp * gmmdev::kFields + plane;
         const bool weight = plane == GMM_PLANE_W_C || plane == GMM_PLANE_W_D;
-        std::vector<uint8_t> tmp((size_t)L.n_pad * L.elem);
+        const size_t run = (size_t)gmmdev::kTile * L.elem;
+        std::vector<uint8_t> tmp((size_t)L.n_tiles * run, 0);
         float_to_plane(src, L.elem, weight, L, c.H, c.W, tmp.data());
-        uint8_t *dst = static_cast<uint8_t *>(arena) + (size_t)pi * L.stride * L.elem;
-        e = cudaMemcpyAsync(dst, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, stream);
+        uint8_t *dst = static_cast<uint8_t *>(arena) + (size_t)pi * run;
+        e = cudaMemcpy2DAsync(dst, L.tile_bytes, tmp.data(), run, run, (size_t)L.n_tiles,
+                              cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess)
             e = cudaStreamSynchronize(stream);
     }

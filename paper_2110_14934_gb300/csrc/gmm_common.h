@@ -23,11 +23,11 @@ struct DeviceGuard {
     ~DeviceGuard();
 };
 
-// Device layout of one camera's state (see gmm_device.cuh).
+// Device layout of one camera's state (tiles of planes, see gmm_device.cuh).
 struct Layout {
-    int w_pad = 0, wpr = 0, elem = 4;
-    int64_t n_pad = 0, stride = 0;
-    size_t planes_bytes = 0, fusion_bytes = 0, total = 0;
+    int w_pad = 0, wpr = 0, elem = 4, planes_per_tile = 0;
+    int64_t n_pad = 0, n_tiles = 0;
+    size_t tile_bytes = 0, planes_bytes = 0, fusion_bytes = 0, total = 0;
 };
 Layout make_layout(int H, int W, int M, int prec);
 

@@ -3,13 +3,18 @@
 // precisions, one mixture step (match, update or replace, re-rank,
 // background test), List-1 fusion, and the bit-packed mask write.
 //
-// State layout in device memory (one camera): M*8 planes, component-major,
-// plane index = 8*i + field with fields {w_c, mu_r, mu_g, mu_b, v_c, w_d,
-// mu_d, v_d}; each plane holds H*w_pad elements (rows padded to a multiple of
-// 32 pixels, so 32 consecutive pixels of a warp map to one mask word) and
-// starts at a multiple of `stride` elements. A warp reads 32 consecutive
-// elements of each plane: one fully used 128-byte line per plane in FP32.
-// The List-1 byte of a pixel lives in a separate H*w_pad byte array.
+// State layout in device memory (one camera). Pixels are numbered in padded
+// row-major order p = row * w_pad + x (rows padded to a multiple of 32 pixels,
+// so the 32 pixels of a warp map to one mask word) and grouped into tiles of
+// kTile = 256 consecutive pixels. Each tile stores its M*8 planes
+// contiguously, component-major: plane 8*i + field (fields w_c, mu_r, mu_g,
+// mu_b, v_c, w_d, mu_d, v_d; i the rank), kTile elements each. Element
+// (plane k, pixel p) sits at ((p / kTile) * 8M + k) * kTile + p % kTile.
+// A warp reads 32 consecutive elements of a plane (one fully used 128-byte
+// line in FP32); the plane offsets of a pixel are compile-time constants
+// from one base address; and a tile's whole state is one contiguous block
+// that a single bulk copy moves. The List-1 byte of a pixel lives in a
+// separate byte array indexed by p (n_tiles * kTile bytes).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -19,8 +24,10 @@
 namespace gmmdev {
 
 constexpr int kFields = 8;
+constexpr int kTile = 256; // pixels per state tile
 enum { F_WC = 0, F_MUR, F_MUG, F_MUB, F_VC, F_WD, F_MUD, F_VD };
 constexpr uint32_t kDepthStarted = 16u;
+constexpr int kStageInputs = 1;
 
 struct StreamPrm {
     float alpha, oma, k2, T, init_var, init_w, v_min, pad;
@@ -29,17 +36,17 @@ struct StreamPrm {
 // Everything one tick of one camera needs; passed by value to the
 // single-camera kernel, read from a device table by the pooled kernel.
 struct CamView {
-    void *planes;          // M*8 planes of `stride` elements
-    uint8_t *fusion;       // H*w_pad List-1 bytes
+    void *planes;          // n_tiles tiles of M*8 planes of kTile elements
+    uint8_t *fusion;       // n_tiles*kTile List-1 bytes, indexed by padded pixel
     const uint8_t *rgb;    // H*W*3, interleaved
     const uint16_t *depth; // H*W, millimetres, 0 = invalid
     uint32_t *mask;        // H*wpr words: fused foreground
     uint32_t *fg_rgb;      // optional colour foreground words (may be null)
     uint32_t *fg_d;        // optional depth foreground words (may be null)
-    int64_t stride;        // plane stride in elements
+    int64_t n_tiles;       // state tiles: ceil(n_pad / kTile)
     int64_t n_pad;         // H*w_pad (< 2^30)
     int H, W, w_pad, wpr;  // wpr = words per mask row = w_pad / 32
-    int M, prec, first, pad;
+    int M, prec, first, flags; // flags: kStageInputs (set by the staged launcher)
     uint32_t wpr_mul, wpr_shift; // n / wpr == umulhi(n, wpr_mul) >> wpr_shift (wpr > 1)
     StreamPrm pc, pd;
 };
@@ -241,7 +248,8 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
                          (float)cv.rgb[3 * q + 2]};
     const uint32_t draw = cv.depth[q];
     const float xd[1] = {(float)draw};
-    const int64_t st = cv.stride;
+    // Element of plane 0 for this pixel; plane k lies k * kTile further on.
+    const int64_t e0 = (int64_t)(p32 / kTile) * (kFields * M * kTile) + (p32 % kTile);
     const void *pl = cv.planes;
 
     Comp<3> c[M];
@@ -262,15 +270,15 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
         fb = cv.fusion[p];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            const int64_t b = (int64_t)(kFields * i) * st + p;
-            c[i].w = S::ldw(pl, b + F_WC * st);
-            c[i].mu[0] = S::ldv(pl, b + F_MUR * st);
-            c[i].mu[1] = S::ldv(pl, b + F_MUG * st);
-            c[i].mu[2] = S::ldv(pl, b + F_MUB * st);
-            c[i].v = S::ldv(pl, b + F_VC * st);
-            d[i].w = S::ldw(pl, b + F_WD * st);
-            d[i].mu[0] = S::ldv(pl, b + F_MUD * st);
-            d[i].v = S::ldv(pl, b + F_VD * st);
+            const int64_t b = e0 + kFields * i * kTile;
+            c[i].w = S::ldw(pl, b + F_WC * kTile);
+            c[i].mu[0] = S::ldv(pl, b + F_MUR * kTile);
+            c[i].mu[1] = S::ldv(pl, b + F_MUG * kTile);
+            c[i].mu[2] = S::ldv(pl, b + F_MUB * kTile);
+            c[i].v = S::ldv(pl, b + F_VC * kTile);
+            d[i].w = S::ldw(pl, b + F_WD * kTile);
+            d[i].mu[0] = S::ldv(pl, b + F_MUD * kTile);
+            d[i].v = S::ldv(pl, b + F_VD * kTile);
         }
         fgc = mixture_step<M, 3>(c, xc, cv.pc);
     }
@@ -294,15 +302,15 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
     void *plw = cv.planes;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-        const int64_t b = (int64_t)(kFields * i) * st + p;
-        S::stw(plw, b + F_WC * st, c[i].w);
-        S::stv(plw, b + F_MUR * st, c[i].mu[0]);
-        S::stv(plw, b + F_MUG * st, c[i].mu[1]);
-        S::stv(plw, b + F_MUB * st, c[i].mu[2]);
-        S::stv(plw, b + F_VC * st, c[i].v);
-        S::stw(plw, b + F_WD * st, d[i].w);
-        S::stv(plw, b + F_MUD * st, d[i].mu[0]);
-        S::stv(plw, b + F_VD * st, d[i].v);
+        const int64_t b = e0 + kFields * i * kTile;
+        S::stw(plw, b + F_WC * kTile, c[i].w);
+        S::stv(plw, b + F_MUR * kTile, c[i].mu[0]);
+        S::stv(plw, b + F_MUG * kTile, c[i].mu[1]);
+        S::stv(plw, b + F_MUB * kTile, c[i].mu[2]);
+        S::stv(plw, b + F_VC * kTile, c[i].v);
+        S::stw(plw, b + F_WD * kTile, d[i].w);
+        S::stv(plw, b + F_MUD * kTile, d[i].mu[0]);
+        S::stv(plw, b + F_VD * kTile, d[i].v);
     }
     cv.fusion[p] = (uint8_t)fb;
     return (fb & 1u) | ((uint32_t)fgc << 1) | ((uint32_t)fgd << 2);

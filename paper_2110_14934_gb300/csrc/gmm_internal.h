@@ -12,8 +12,8 @@ namespace gmmhost {
 cudaError_t launch_tick(const gmmdev::CamView &cv, int threads, cudaStream_t s);
 
 // Staged single-camera tick (bulk-copy pipeline through shared memory).
-// variant: tile shape (0: 256 px x 2 stages, 1: 256 x 3, 2: 128 x 3,
-// 3: 128 x 4); ctas_per_sm: 0 = as many as fit. status: device word that
+// variant: pipeline depth (0..3: 2..5 stages of one 256-pixel tile);
+// ctas_per_sm: 0 = as many as fit. status: device word that
 // gets bit 0 set if a pipeline wait runs out. Not for first ticks.
 cudaError_t launch_tick_staged(const gmmdev::CamView &cv, int variant, int ctas_per_sm,
                                int *status, cudaStream_t s);

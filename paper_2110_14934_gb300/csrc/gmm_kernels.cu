@@ -47,7 +47,7 @@ __device__ __forceinline__ void pool_tile(const CamView &cv, int64_t p0, int64_t
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(512) k_pool_tick(const PoolArgs a) {
+__global__ void __launch_bounds__(256, 3) k_pool_tick(const PoolArgs a) {
     __shared__ CamView s_cv;
     __shared__ int64_t s_tile;
     __shared__ int s_job;

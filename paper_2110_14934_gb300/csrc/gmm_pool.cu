@@ -310,6 +310,21 @@ int gmm_pool_submit(gmm_pool_t *p, int cam, const uint8_t *rgb8, const uint16_t 
     return GMM_OK;
 }
 
+int gmm_pool_submit_many(gmm_pool_t *p, int n, const int *cams, const uint8_t *const *rgb8,
+                         const uint16_t *const *depth16, uint32_t *const *mask_out) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_submit_many: null pool");
+    if (n < 0 || (n > 0 && (!cams || !rgb8 || !depth16 || !mask_out)))
+        return fail(GMM_EINVAL, "gmm_pool_submit_many: bad arrays");
+    for (int i = 0; i < n; ++i) {
+        const int rc = gmm_pool_submit(p, cams[i], rgb8[i], depth16[i], mask_out[i], nullptr,
+                                       nullptr);
+        if (rc != GMM_OK)
+            return rc;
+    }
+    return GMM_OK;
+}
+
 int gmm_pool_tick(gmm_pool_t *p) {
     if (!p)
         return fail(GMM_EINVAL, "gmm_pool_tick: null pool");
@@ -335,8 +350,8 @@ int gmm_pool_set_launch(gmm_pool_t *p, int threads, int ctas_per_sm, int tile_pi
     const int t = threads ? threads : p->threads;
     const int c = ctas_per_sm ? ctas_per_sm : p->ctas_per_sm;
     const int tp = tile_pixels ? tile_pixels : p->tile_pixels;
-    if (t < 64 || t > 512 || t % 32)
-        return fail(GMM_EINVAL, "gmm_pool_set_launch: threads must be 64..512, a multiple of 32");
+    if (t < 64 || t > 256 || t % 32)
+        return fail(GMM_EINVAL, "gmm_pool_set_launch: threads must be 64..256, a multiple of 32");
     if (c < 0 || c > 32)
         return fail(GMM_EINVAL, "gmm_pool_set_launch: ctas_per_sm must be in [0, 32]");
     if (tp < t || tp % t || tp > (1 << 24))
@@ -401,7 +416,7 @@ int gmm_pool_autotune(gmm_pool_t *p, int iters, int *threads_out, int *ctas_out,
     p->use_graph = false;
     int best_t = saved_t, best_c = saved_c, best_tp = saved_tp;
     float best_ms = -1.f;
-    const int cand_threads[] = {128, 256, 512};
+    const int cand_threads[] = {128, 256};
     const int cand_tiles[] = {2048, 8192, 32768};
     int rc = GMM_OK;
     for (int t : cand_threads) {

@@ -1,13 +1,15 @@
 // Staged tick kernel: persistent CTAs stream tiles of the state through
 // shared memory with 1-D bulk copies (TMA engine) in a multi-stage pipeline.
 //
-// Per tile of TP padded pixels, one thread issues 8*M plane copies plus the
-// List-1 bytes into a stage buffer (an mbarrier counts the bytes), the whole
-// CTA computes one pixel per thread out of shared memory, and the same thread
-// writes the stage back with bulk stores. Loads for the next ST-1 tiles are
-// in flight while a tile is computed, so the HBM traffic no longer waits on
-// the arithmetic, and the per-thread instruction stream holds no global
-// address arithmetic.
+// A state tile (256 pixels, all 8*M planes) is one contiguous block in HBM.
+// Per tile one thread issues a single bulk copy of that block, one of the
+// tile's List-1 bytes and, when the frame rows allow it, one each for the
+// tile's RGB and depth bytes, into a stage buffer (an mbarrier counts the
+// bytes); the whole CTA computes one pixel per thread out of shared memory;
+// the same thread writes the stage back with two bulk stores. Loads for the
+// next ST-1 tiles are in flight while a tile is computed, so the HBM traffic
+// does not wait on the arithmetic, and the per-thread instruction stream
+// holds no global address arithmetic.
 //
 // With the state in shared memory the re-ranking needs no sorting network:
 // each component's stable rank comes from M(M-1)/2 key comparisons and the
@@ -189,13 +191,13 @@ __device__ __forceinline__ int staged_mixture_step(uint8_t *st, int f0, int t,
 }
 
 // One pixel (column t of the stage); returns fused | colour << 1 | depth << 2.
-template <int M, int PREC, int TP>
+template <int M, int PREC>
 __device__ __forceinline__ uint32_t staged_pixel(uint8_t *st, int t, const CamView &cv,
                                                  const float (&xc)[3], uint32_t draw) {
-    using A = Smem<PREC, TP>;
-    uint8_t *fus = st + kFields * M * TP * A::kBytes;
+    using A = Smem<PREC, kTile>;
+    uint8_t *fus = st + kFields * M * kTile * A::kBytes;
     uint32_t fb = fus[t];
-    const int fgc = staged_mixture_step<M, 3, PREC, TP>(st, F_WC, t, xc, cv.pc);
+    const int fgc = staged_mixture_step<M, 3, PREC, kTile>(st, F_WC, t, xc, cv.pc);
     int fgd;
     if (draw == 0u) {
         fgd = fgc; // no reading: depth model untouched, depth answer = colour
@@ -211,27 +213,31 @@ __device__ __forceinline__ uint32_t staged_pixel(uint8_t *st, int t, const CamVi
         fgd = 0;
     } else {
         const float xd[1] = {(float)draw};
-        fgd = staged_mixture_step<M, 1, PREC, TP>(st, F_WD, t, xd, cv.pd);
+        fgd = staged_mixture_step<M, 1, PREC, kTile>(st, F_WD, t, xd, cv.pd);
     }
     fb = fuse_list1(fgc, fgd, fb);
     fus[t] = (uint8_t)fb;
     return (fb & 1u) | ((uint32_t)fgc << 1) | ((uint32_t)fgd << 2);
 }
 
-template <int M, int PREC, int TP, int ST>
-__global__ void __launch_bounds__(TP) k_tick_staged(const CamView cv, int *status) {
-    using A = Smem<PREC, TP>;
-    constexpr int EB = A::kBytes;
-    constexpr int NPL = kFields * M;
-    constexpr uint32_t PLANE = TP * EB;
-    constexpr uint32_t STAGE = NPL * PLANE + TP;
-    static_assert(PLANE % 16 == 0 && STAGE % 16 == 0, "bulk copies need 16-byte granules");
+// One CTA of kTile threads per state tile in flight. A stage holds one tile:
+// its 8M planes (one contiguous block in HBM, moved by one bulk copy), its
+// List-1 bytes and, when cv.flags has kStageInputs, its RGB and depth bytes.
+template <int M, int PREC, int ST>
+__global__ void __launch_bounds__(kTile) k_tick_staged(const CamView cv, int *status) {
+    using A = Smem<PREC, kTile>;
+    constexpr uint32_t STATE = kFields * M * kTile * A::kBytes; // one tile of planes
+    constexpr uint32_t FUS = STATE;                            // List-1 bytes
+    constexpr uint32_t RGB = FUS + kTile;                      // 3 bytes per pixel
+    constexpr uint32_t DEP = RGB + 3 * kTile;                  // 2 bytes per pixel
+    constexpr uint32_t STAGE = DEP + 2 * kTile;
+    static_assert(STATE % 16 == 0 && STAGE % 16 == 0, "bulk copies need 16-byte granules");
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t full[ST];
 
     const int tid = threadIdx.x;
-    const int64_t n_tiles = (cv.n_pad + TP - 1) / TP;
-    const size_t pstride = (size_t)cv.stride * EB; // bytes between planes in HBM
+    const int64_t n_tiles = cv.n_tiles;
+    const bool stage_in = (cv.flags & kStageInputs) != 0;
     const uint8_t *gsrc = static_cast<const uint8_t *>(cv.planes);
     uint8_t *gdst = static_cast<uint8_t *>(cv.planes);
     uint32_t pending = 0; // thread 0: stages with a load in flight
@@ -245,14 +251,16 @@ __global__ void __launch_bounds__(TP) k_tick_staged(const CamView cv, int *statu
     __syncthreads();
 
     auto issue_load = [&](int64_t tile, int s) {
-        const int64_t p0 = tile * TP;
-        const uint32_t npx = (uint32_t)min((int64_t)TP, cv.n_pad - p0);
-        const uint32_t nb = npx * EB;
+        const int64_t p0 = tile * kTile;
+        const uint32_t npx = (uint32_t)min((int64_t)kTile, cv.n_pad - p0);
         uint8_t *dst = smem + s * STAGE;
-        gmmtma::mbar_arrive_expect_tx(&full[s], NPL * nb + npx);
-        for (int k = 0; k < NPL; ++k)
-            gmmtma::bulk_load(dst + k * PLANE, gsrc + k * pstride + p0 * EB, nb, &full[s]);
-        gmmtma::bulk_load(dst + NPL * PLANE, cv.fusion + p0, npx, &full[s]);
+        gmmtma::mbar_arrive_expect_tx(&full[s], STATE + kTile + (stage_in ? 5u * npx : 0u));
+        gmmtma::bulk_load(dst, gsrc + (size_t)tile * STATE, STATE, &full[s]);
+        gmmtma::bulk_load(dst + FUS, cv.fusion + p0, kTile, &full[s]);
+        if (stage_in) {
+            gmmtma::bulk_load(dst + RGB, cv.rgb + 3 * p0, 3 * npx, &full[s]);
+            gmmtma::bulk_load(dst + DEP, cv.depth + p0, 2 * npx, &full[s]);
+        }
         pending |= 1u << s;
     };
 
@@ -269,18 +277,21 @@ __global__ void __launch_bounds__(TP) k_tick_staged(const CamView cv, int *statu
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++j) {
         const int s = j % ST;
         const uint32_t parity = (uint32_t)(j / ST) & 1u;
-        const int64_t p0 = tile * TP;
+        const int64_t p0 = tile * kTile;
         const uint32_t p = (uint32_t)(p0 + tid);
         const bool in = (int64_t)p < cv.n_pad;
-        // Frame inputs straight from HBM, issued before the stage wait.
+        uint8_t *stg = smem + s * STAGE;
+        // Row of the pixel; frame inputs come from the stage or, when they are
+        // not staged, straight from HBM before the stage wait.
+        uint32_t row = 0, x = 0;
+        bool valid = false;
         float xc[3] = {0.f, 0.f, 0.f};
         uint32_t draw = 0u;
-        bool valid = false;
         if (in) {
-            const uint32_t row = div_wpr(p >> 5, cv);
-            const uint32_t x = p - row * (uint32_t)cv.w_pad;
+            row = div_wpr(p >> 5, cv);
+            x = p - row * (uint32_t)cv.w_pad;
             valid = x < (uint32_t)cv.W;
-            if (valid) {
+            if (valid && !stage_in) {
                 const int64_t q = (int64_t)row * cv.W + x;
                 xc[0] = (float)cv.rgb[3 * q];
                 xc[1] = (float)cv.rgb[3 * q + 1];
@@ -295,20 +306,23 @@ __global__ void __launch_bounds__(TP) k_tick_staged(const CamView cv, int *statu
         }
         if (tid == 0)
             pending &= ~(1u << s);
-        uint8_t *stg = smem + s * STAGE;
         uint32_t bits = 0u;
-        if (valid)
-            bits = staged_pixel<M, PREC, TP>(stg, tid, cv, xc, draw);
-        if (in) // whole warps: n_pad and TP are multiples of 32
+        if (valid) {
+            if (stage_in) {
+                xc[0] = (float)stg[RGB + 3 * tid];
+                xc[1] = (float)stg[RGB + 3 * tid + 1];
+                xc[2] = (float)stg[RGB + 3 * tid + 2];
+                draw = reinterpret_cast<const uint16_t *>(stg + DEP)[tid];
+            }
+            bits = staged_pixel<M, PREC>(stg, tid, cv, xc, draw);
+        }
+        if (in) // whole warps: n_pad and kTile are multiples of 32
             write_mask_words(cv, p >> 5, bits);
         gmmtma::fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
-            const uint32_t npx = (uint32_t)min((int64_t)TP, cv.n_pad - p0);
-            const uint32_t nb = npx * EB;
-            for (int k = 0; k < NPL; ++k)
-                gmmtma::bulk_store(gdst + k * pstride + p0 * EB, stg + k * PLANE, nb);
-            gmmtma::bulk_store(cv.fusion + p0, stg + NPL * PLANE, npx);
+            gmmtma::bulk_store(gdst + (size_t)tile * STATE, stg, STATE);
+            gmmtma::bulk_store(cv.fusion + p0, stg + FUS, kTile);
             gmmtma::bulk_commit();
             const int64_t next = tile + (int64_t)ST * gridDim.x;
             if (next < n_tiles) {
@@ -331,19 +345,19 @@ __global__ void __launch_bounds__(TP) k_tick_staged(const CamView cv, int *statu
     }
 }
 
-template <int M, int PREC, int TP, int ST>
+template <int M, int PREC, int ST>
 cudaError_t launch_staged_t(const CamView &cv, int ctas_per_sm, int *status, cudaStream_t s) {
     constexpr int EB = PREC == 0 ? 4 : 2;
-    constexpr size_t smem = (size_t)ST * (kFields * M * TP * EB + TP);
+    constexpr size_t smem = (size_t)ST * (kFields * M * kTile * EB + 6 * kTile);
     static bool configured = false;
     static int max_per_sm = 1;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tick_staged<M, PREC, TP, ST>,
+        cudaError_t e = cudaFuncSetAttribute(k_tick_staged<M, PREC, ST>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm, k_tick_staged<M, PREC, TP, ST>,
-                                                          TP, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm, k_tick_staged<M, PREC, ST>,
+                                                          kTile, smem);
         if (e != cudaSuccess)
             return e;
         if (max_per_sm < 1)
@@ -351,43 +365,48 @@ cudaError_t launch_staged_t(const CamView &cv, int ctas_per_sm, int *status, cud
         configured = true;
     }
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < max_per_sm) ? ctas_per_sm : max_per_sm;
-    const int64_t n_tiles = (cv.n_pad + TP - 1) / TP;
     int64_t grid = (int64_t)gmmhost::num_sms() * per_sm;
-    if (grid > n_tiles)
-        grid = n_tiles;
-    k_tick_staged<M, PREC, TP, ST><<<(unsigned)grid, TP, smem, s>>>(cv, status);
+    if (grid > cv.n_tiles)
+        grid = cv.n_tiles;
+    k_tick_staged<M, PREC, ST><<<(unsigned)grid, kTile, smem, s>>>(cv, status);
     return cudaGetLastError();
 }
 
-template <int PREC, int TP, int ST>
+template <int PREC, int ST>
 cudaError_t launch_staged_m(const CamView &cv, int ctas, int *status, cudaStream_t s) {
     switch (cv.M) {
-    case 3: return launch_staged_t<3, PREC, TP, ST>(cv, ctas, status, s);
-    case 4: return launch_staged_t<4, PREC, TP, ST>(cv, ctas, status, s);
-    case 5: return launch_staged_t<5, PREC, TP, ST>(cv, ctas, status, s);
+    case 3: return launch_staged_t<3, PREC, ST>(cv, ctas, status, s);
+    case 4: return launch_staged_t<4, PREC, ST>(cv, ctas, status, s);
+    case 5: return launch_staged_t<5, PREC, ST>(cv, ctas, status, s);
     }
     return cudaErrorInvalidValue;
 }
 
-template <int TP, int ST>
+template <int ST>
 cudaError_t launch_staged_p(const CamView &cv, int ctas, int *status, cudaStream_t s) {
-    return cv.prec == 0 ? launch_staged_m<0, TP, ST>(cv, ctas, status, s)
-                        : launch_staged_m<1, TP, ST>(cv, ctas, status, s);
+    return cv.prec == 0 ? launch_staged_m<0, ST>(cv, ctas, status, s)
+                        : launch_staged_m<1, ST>(cv, ctas, status, s);
 }
 
 } // namespace
 
 namespace gmmhost {
 
-cudaError_t launch_tick_staged(const CamView &cv, int variant, int ctas_per_sm, int *status,
+cudaError_t launch_tick_staged(const CamView &cv_in, int variant, int ctas_per_sm, int *status,
                                cudaStream_t s) {
-    if (cv.n_pad == 0)
+    if (cv_in.n_pad == 0)
         return cudaSuccess;
+    CamView cv = cv_in;
+    // Frame bytes are staged with the state when every tile's slice of them
+    // is contiguous and 16-byte aligned: unpadded rows and aligned bases.
+    if (cv.W == cv.w_pad && reinterpret_cast<uintptr_t>(cv.rgb) % 16 == 0 &&
+        reinterpret_cast<uintptr_t>(cv.depth) % 16 == 0)
+        cv.flags |= kStageInputs;
     switch (variant) {
-    case 0: return launch_staged_p<256, 2>(cv, ctas_per_sm, status, s);
-    case 1: return launch_staged_p<256, 3>(cv, ctas_per_sm, status, s);
-    case 2: return launch_staged_p<128, 3>(cv, ctas_per_sm, status, s);
-    case 3: return launch_staged_p<128, 4>(cv, ctas_per_sm, status, s);
+    case 0: return launch_staged_p<2>(cv, ctas_per_sm, status, s);
+    case 1: return launch_staged_p<3>(cv, ctas_per_sm, status, s);
+    case 2: return launch_staged_p<4>(cv, ctas_per_sm, status, s);
+    case 3: return launch_staged_p<5>(cv, ctas_per_sm, status, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -94,11 +94,12 @@ def test_null_handles_are_rejected():
 
 def test_sizes():
     assert [G.mask_words_per_row(w) for w in (1, 31, 32, 33, 640, 1920)] == [1, 1, 1, 2, 20, 60]
-    # FP32: 8 planes * M * 4 bytes per padded pixel (planes 256-byte aligned) + 1 fusion byte
+    # 256-pixel tiles of 8*M planes (4 or 2 bytes each) plus one List-1 byte per tiled pixel
     n = 480 * 640
     assert G.state_bytes(480, 640, 3, G.PREC_F32) == 3 * 8 * n * 4 + n
     assert G.state_bytes(1080, 1920, 5, G.PREC_F16) == 5 * 8 * 1080 * 1920 * 2 + 1080 * 1920
-    assert G.state_bytes(1, 1, 3, G.PREC_F32) == 24 * 128 * 4 + 256
+    assert G.state_bytes(1, 1, 3, G.PREC_F32) == 24 * 256 * 4 + 256
+    assert G.state_bytes(3, 33, 4, G.PREC_F16) == 32 * 256 * 2 + 256
     assert G.state_bytes(10, 10, 2, G.PREC_F32) == 0
 
 

@@ -86,7 +86,7 @@ def test_pool_equals_alone_in_a_changing_mix():
         assert np.array_equal(a[key], b[key]), key
 
 
-@pytest.mark.parametrize("launch", [(128, 1, 128), (512, 2, 2048), (256, 0, 32768)])
+@pytest.mark.parametrize("launch", [(128, 1, 128), (256, 2, 2048), (256, 0, 32768)])
 def test_pool_graph_and_launch_shapes(launch):
     n = 6
     frames = _frames(n)

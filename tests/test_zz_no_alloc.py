@@ -33,15 +33,16 @@ def _caller_plane(state, H, W, M, prec, comp, field):
     """Decode one plane of the caller-owned state (layout of gmm.h)."""
     import torch
     w_pad = ((W + 31) // 32) * 32
-    S = ((H * w_pad + 127) // 128) * 128
+    n_tiles = (H * w_pad + 255) // 256
     if prec == G.PREC_F32:
         flat = state.view(torch.float32)
     elif field in (G.PLANE_W_C, G.PLANE_W_D):
         flat = state.view(torch.bfloat16)
     else:
         flat = state.view(torch.float16)
-    k = 8 * comp + field
-    return flat[k * S:k * S + H * w_pad].float().reshape(H, w_pad)[:, :W].cpu().numpy()
+    tiles = flat[:n_tiles * 8 * M * 256].reshape(n_tiles, 8 * M, 256)
+    plane = tiles[:, 8 * comp + field, :].reshape(-1)[:H * w_pad]
+    return plane.float().reshape(H, w_pad)[:, :W].cpu().numpy()
 
 
 @pytest.mark.parametrize("H,W,M,prec", [(45, 83, 3, G.PREC_F32), (120, 160, 5, G.PREC_F32),

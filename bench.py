@@ -710,6 +710,10 @@ def main(argv=None):
     ap.add_argument("--kernel", choices=sorted(KERNELS), default="direct")
     ap.add_argument("--variant", type=int, default=0, help="staged tile shape 0-3")
     ap.add_argument("--ctas", type=int, default=0, help="staged CTAs per SM (0: as many as fit)")
+    ap.add_argument("--precision", choices=["default", "f32", "f16"], default="default",
+                    help="override the workload's state storage precision")
+    ap.add_argument("--cams-per-res", type=int, default=0,
+                    help="pooled workloads: cameras per resolution (0: the workload's 16)")
     ap.add_argument("--no-graph", action="store_true", help="pooled workloads: no CUDA graph")
     ap.add_argument("--no-autotune", action="store_true", help="pooled workloads: default launch")
     ap.add_argument("--frames", type=int, default=0,
@@ -719,7 +723,13 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.precision != "default":
+        wl["prec"] = 0 if args.precision == "f32" else 1
+        wl["name"] += f" [state overridden: {args.precision}]"
+    if args.cams_per_res and wl.get("pool"):
+        wl["cams_per_res"] = args.cams_per_res
+        wl["name"] += f" [{args.cams_per_res} cameras per resolution]"
     if args.impl == "reference":
         return run_reference(args, wl)
     if wl.get("pool"):

@@ -140,7 +140,9 @@ template <> __device__ __forceinline__ void rank_sort<5, 1>(Comp<1> (&c)[5]) { n
 
 // One tick of one mixture at one pixel (§III.A). The components are in rank
 // order on entry and on exit. Returns the stream's foreground bit.
-template <int M, int D>
+// kSkipSorted: let a warp skip the sorting network when it would change
+// nothing (pays where issue slots, not HBM, bound the kernel).
+template <int M, int D, bool kSkipSorted>
 __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D],
                                             const StreamPrm &p) {
     // Match: first component, in rank order, within k standard deviations.
@@ -196,8 +198,17 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
         c[i].key = c[i].w * rsqrtf(c[i].v);
     }
 
-    // Re-rank by w / sigma (stable), then the background test.
-    rank_sort<M, D>(c);
+    // Re-rank by w / sigma (stable), then the background test. When every
+    // lane's components are already in non-increasing key order (the usual
+    // case: a background pixel matches its best component and the others
+    // decay by the same factor), the stable network would leave them as they
+    // are, so the warp skips it.
+    bool sorted = true;
+#pragma unroll
+    for (int i = 1; i < M; ++i)
+        sorted = sorted && !(c[i].key > c[i - 1].key);
+    if (!kSkipSorted || __any_sync(__activemask(), !sorted))
+        rank_sort<M, D>(c);
     int rank = 0, B = M;
     float acc = 0.f;
 #pragma unroll
@@ -235,7 +246,7 @@ __device__ __forceinline__ uint32_t fuse_list1(int fgc, int fgd, uint32_t fb) {
 // ------------------------------------------------------------ one pixel
 // p: padded linear pixel index (row * w_pad + x). Returns bit 0 fused label,
 // bit 1 colour foreground, bit 2 depth foreground (all 0 for padding).
-template <int M, int PREC>
+template <int M, int PREC, bool kSkipSorted>
 __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) {
     using S = Storage<PREC>;
     const uint32_t p32 = (uint32_t)p;
@@ -280,7 +291,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
             d[i].mu[0] = S::ldv(pl, b + F_MUD * kTile);
             d[i].v = S::ldv(pl, b + F_VD * kTile);
         }
-        fgc = mixture_step<M, 3>(c, xc, cv.pc);
+        fgc = mixture_step<M, 3, kSkipSorted>(c, xc, cv.pc);
     }
 
     if (draw == 0u) {
@@ -295,7 +306,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
         fb |= kDepthStarted;
         fgd = 0;
     } else {
-        fgd = mixture_step<M, 1>(d, xd, cv.pd);
+        fgd = mixture_step<M, 1, kSkipSorted>(d, xd, cv.pd);
     }
     fb = fuse_list1(fgc, fgd, fb);
 

@@ -18,11 +18,11 @@ namespace {
 
 // ------------------------------------------------------------ single camera
 template <int M, int PREC>
-__global__ void __launch_bounds__(256) k_tick(const CamView cv) {
+__global__ void __launch_bounds__(256, PREC == 0 ? 1 : 4) k_tick(const CamView cv) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= cv.n_pad) // n_pad is a multiple of 32: whole warps leave
         return;
-    const uint32_t bits = process_pixel<M, PREC>(cv, p);
+    const uint32_t bits = process_pixel<M, PREC, PREC != 0>(cv, p);
     write_mask_words(cv, p >> 5, bits);
 }
 
@@ -41,13 +41,13 @@ template <int M, int PREC>
 __device__ __forceinline__ void pool_tile(const CamView &cv, int64_t p0, int64_t p1) {
     for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         // p1 - p0 is a multiple of 32 and blockDim too: warps stay whole.
-        const uint32_t bits = process_pixel<M, PREC>(cv, p);
+        const uint32_t bits = process_pixel<M, PREC, true>(cv, p);
         write_mask_words(cv, p >> 5, bits);
     }
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(256, 3) k_pool_tick(const PoolArgs a) {
+__global__ void __launch_bounds__(256, PREC == 0 ? 3 : 4) k_pool_tick(const PoolArgs a) {
     __shared__ CamView s_cv;
     __shared__ int64_t s_tile;
     __shared__ int s_job;

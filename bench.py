@@ -48,6 +48,13 @@ WORKLOADS = {
                     "arithmetic), 1000 ticks over 300 resident frames per camera",
                pool=True, cams_per_res=16, frames=300, prec=1, M=5),
 }
+WORKLOADS["c4"] = dict(
+    name="serving: 256 cameras (64 each at 320x240, 640x480, 1280x720, 1920x1080), M from {3,5} "
+         "by seed, FP16/BF16 state, sessions joining and leaving on a seeded Poisson schedule "
+         "(mean session 600 frames, 75% of cameras live on average), 30 fps per camera with "
+         "+-2 ms jitter, 80 GB memory budget, continuous batching",
+    serve=True, cams_per_res=64, prec=1, M=5, fps=30.0, session_frames=600, live_fraction=0.75,
+    budget_gb=80.0, duration_s=20.0, tight_budget_gb=8.0, tight_duration_s=8.0, frames=8)
 CAMERA_RESOLUTIONS = [(240, 320), (480, 640), (720, 1280), (1080, 1920)]
 KERNELS = {"staged": 0, "direct": 1}
 METRIC = "Mpixel-frames/s (RGB+depth GMM+fusion)"
@@ -233,7 +240,7 @@ def oracle_rate(wl: dict, frames: int, rows: int, seed: int):
 def reference_cameras(wl):
     """(H, W, M, seed, scene kind) the reference arm samples: the workload's
     camera, or one camera per resolution of a many-camera mix."""
-    if wl.get("pool"):
+    if wl.get("pool") or wl.get("serve"):
         mix = camera_mix(wl["cams_per_res"], 0)
         return [(H, W, M, seed, 1) for (H, W, M, seed) in mix[::wl["cams_per_res"]]]
     return [(wl["H"], wl["W"], wl["M"], 1, wl["kind"])]
@@ -272,7 +279,7 @@ def run_reference(args, wl):
     value = args.steps * sum(b[4] for b in bands) / dt / 1e6
     sample = "each step: " + "; ".join(descr) + " (one frame each), FP64, 1 thread"
     cfg = (pool_config(args.workload, wl, world, camera_mix(wl["cams_per_res"], 0), None, None)
-           if wl.get("pool") else config_dict(args.workload, wl, world))
+           if (wl.get("pool") or wl.get("serve")) else config_dict(args.workload, wl, world))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
@@ -390,7 +397,7 @@ def run_gmm(args, wl):
                          "peak_source": peak_src, "algorithmic_bytes_per_px": bpp,
                          "kernel": (f"k_tick_staged<M={M},{'f32' if prec == 0 else 'f16'}>"
                                     f" variant {args.variant}" if args.kernel == "staged" else
-                                    f"k_tick<M={M},{'f32' if prec == 0 else 'f16'}>")},
+                                    f"k_tick_{'f32' if prec == 0 else 'f16'}<M={M}>")},
             "latency_ms": {"tick_p50": pct(tick_sorted, 50), "tick_p99": pct(tick_sorted, 99),
                            "e2e_p50": e2e["lat_p50"], "e2e_p99": e2e["lat_p99"]},
             "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
@@ -644,6 +651,201 @@ def run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, steps, warmup, 
             "d2h": sum(H * G.mask_words_per_row(W) * 4 for (H, W, _, _) in cams)}
 
 
+# ---------------------------------------------------------------- serving
+def serving_schedule(n_cams, duration, fps, session_s, live_fraction, seed):
+    """Seeded session and frame schedule: every camera alternates idle gaps
+    and sessions, both exponential (Poisson joins and leaves), with mean
+    session session_s and mean gap chosen for the given live fraction; a
+    live camera offers frames every 1/fps s with +-2 ms uniform jitter.
+    Returns time-sorted events (t, kind, cam, k) with kind 0 = join,
+    1 = frame k of the session, 2 = leave."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    gap_s = session_s * (1.0 - live_fraction) / live_fraction
+    ev = []
+    for c in range(n_cams):
+        live = rng.random() < live_fraction
+        t = 0.0
+        while t < duration:
+            if live:
+                end = min(duration, t + rng.exponential(session_s))
+                ev.append((t, 0, c, 0))
+                k = 0
+                while True:
+                    tf = t + k / fps + rng.uniform(-0.002, 0.002)
+                    if tf >= end:
+                        break
+                    ev.append((max(t, tf), 1, c, k))
+                    k += 1
+                ev.append((end, 2, c, 0))
+                t = end
+            else:
+                t += rng.exponential(gap_s)
+            live = not live
+    ev.sort(key=lambda e: (e[0], e[1]))
+    return ev
+
+
+def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_depth=4):
+    """Drive a Server through a seeded schedule in real time; returns stats."""
+    import queue as pyqueue
+
+    import numpy as np
+    srv = G.Server(budget_bytes=budget_bytes, precision=wl["prec"], max_cams=len(cams),
+                   queue_depth=queue_depth)
+    events = serving_schedule(len(cams), duration, wl["fps"], wl["session_frames"] / wl["fps"],
+                              wl["live_fraction"], seed)
+    n_slot = queue_depth + 4
+    masks = {}
+    live = {}          # camera -> server id of its current session
+    slot_ticket = {}   # (camera, slot) -> ticket using that mask buffer
+    rel_q = pyqueue.Queue()
+    rel_err = []
+
+    def releaser():
+        while True:
+            sid = rel_q.get()
+            if sid is None:
+                return
+            try:
+                srv.release(sid, 60000)
+            except Exception as e:  # reported, not fatal to the run
+                rel_err.append(str(e))
+
+    import threading as th
+    rt = th.Thread(target=releaser, daemon=True)
+    rt.start()
+    tickets, lag = [], []
+    t0 = srv.now() + 0.5
+    for (t, kind, c, k) in events:
+        due = t0 + t
+        while True:
+            d = due - srv.now()
+            if d <= 0:
+                break
+            time.sleep(d - 0.0005) if d > 0.001 else None
+        H, W, M, _ = cams[c]
+        if kind == 0:
+            try:
+                live[c] = srv.admit(H, W, M, **PARAMS)
+            except G.GMMError as e:
+                if e.code != G.EBUDGET:
+                    raise
+        elif kind == 2:
+            sid = live.pop(c, None)
+            if sid is not None:
+                rel_q.put(sid)
+        elif c in live:
+            ri = CAMERA_RESOLUTIONS.index((H, W))
+            rgb_h, dep_h = ring[ri]
+            slot = k % n_slot
+            old = slot_ticket.get((c, slot))
+            if old is not None and not srv.done(old):
+                srv.wait(old, 60000)
+            if (c, slot) not in masks:
+                masks[(c, slot)] = torch.empty((H, G.mask_words_per_row(W)),
+                                               dtype=torch.int32).pin_memory()
+            f = (k + c) % rgb_h.shape[0]
+            lag.append((srv.now() - due) * 1e3)
+            try:
+                tk = srv.push(live[c], rgb_h[f], dep_h[f], masks[(c, slot)], t_arrival=due)
+                tickets.append(tk)
+                slot_ticket[(c, slot)] = tk
+            except G.GMMError as e:
+                if e.code != G.EBUDGET:
+                    raise
+    for tk in tickets:
+        srv.wait(tk, 60000)
+    t_end = srv.now()
+    for sid in list(live.values()):
+        rel_q.put(sid)
+    rel_q.put(None)
+    rt.join()
+    st = srv.stats()
+    lat = np.sort(srv.latencies_ms())
+    srv.close()
+    lag.sort()
+    return st, lat, t_end - t0, lag, rel_err
+
+
+def run_serving(args, wl):
+    import numpy as np  # noqa: F401  (used by the helpers)
+    import torch
+    import paper_2110_14934_gb300 as G
+    import synth
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cams = camera_mix(wl["cams_per_res"], rank)
+    nf = wl["frames"]
+    ring = []
+    for ri, (H, W) in enumerate(CAMERA_RESOLUTIONS):
+        r, d, _ = synth.frames_device(synth.scene(rank_seed(5000 + ri, rank), H, W, 1), 0, nf,
+                                      device=dev, with_gt=False)
+        ring.append((r.cpu().pin_memory(), d.cpu().pin_memory()))
+    duration = args.serve_seconds or wl["duration_s"]
+    barrier(world, dev)
+    st, lat, wall, lag, rel_err = serve_run(G, torch, cams, ring, wl,
+                                            int(wl["budget_gb"] * 1e9), duration, 2021 + rank)
+    wall = reduce_max(wall, world, dev)
+    pixels = st["pixels"]
+    total_px = pixels * world  # weak scaling: every rank serves its own cameras
+    value = total_px / wall / 1e6
+    st2, lat2, _, _, _ = serve_run(G, torch, cams, ring, wl, int(wl["tight_budget_gb"] * 1e9),
+                                   wl["tight_duration_s"], 77 + rank)
+    mean_bpp = sum(H * W * bytes_per_pixel(M, wl["prec"]) for (H, W, M, _) in cams) / \
+        sum(H * W for (H, W, _, _) in cams)
+    achieved = pixels * mean_bpp / wall / 1e9
+    peak, peak_src = measured_hbm_peak()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": st["ticks"], "warmup": 0, "ms_per_step": wall / max(st["ticks"], 1) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"c4: {wl['name']}", "cameras_per_gpu": len(cams),
+                       "duration_s": duration, "state": "f16/bf16",
+                       "parallelism": f"camera-sharded x{world}"},
+            "latency_ms": {"p50": fnum(pct(list(lat), 50)), "p99": fnum(pct(list(lat), 99)),
+                           "p999": fnum(pct(list(lat), 99.9)),
+                           "max": float(lat[-1]) if lat.size else None,
+                           "what": "frame arrival to fused mask in host memory"},
+            "serving": {"frames_completed": st["completed"], "frames_dropped": st["dropped"],
+                        "sessions_admitted": st["admitted"], "admissions_rejected": st["rejected"],
+                        "ticks": st["ticks"], "mean_frames_per_tick": st["completed"] / max(st["ticks"], 1),
+                        "driver_lag_ms_p99": fnum(pct(lag, 99)), "release_errors": len(rel_err),
+                        "budget_gb": wl["budget_gb"]},
+            "tight_budget": {"budget_gb": wl["tight_budget_gb"], "duration_s": wl["tight_duration_s"],
+                             "sessions_admitted": st2["admitted"], "admissions_rejected": st2["rejected"],
+                             "frames_completed": st2["completed"],
+                             "latency_ms_p99": fnum(pct(list(lat2), 99))},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "note": "offered-load bound: the cameras offer far less than the GPU "
+                                 "can serve, so this is utilisation, not a kernel limit"},
+            "e2e": {"value": value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(pixels * 5 / max(st["ticks"], 1)),
+                    "d2h_bytes_per_step": int(pixels / 8 / max(st["ticks"], 1)),
+                    "path": "page-locked host frames -> gmm_server_push -> masks in host memory"},
+            "cpu_baseline": None,
+            "gpu_launches": st["ticks"],
+            "clocks": None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def fnum(x):
+    return None if x is None else float(x)
+
+
 def pct(sorted_vals, p):
     if not sorted_vals:
         return None
@@ -715,6 +917,8 @@ def main(argv=None):
     ap.add_argument("--cams-per-res", type=int, default=0,
                     help="pooled workloads: cameras per resolution (0: the workload's 16)")
     ap.add_argument("--no-graph", action="store_true", help="pooled workloads: no CUDA graph")
+    ap.add_argument("--serve-seconds", type=float, default=0.0,
+                    help="serving workload: simulated seconds (0: the workload's 20)")
     ap.add_argument("--no-autotune", action="store_true", help="pooled workloads: default launch")
     ap.add_argument("--frames", type=int, default=0,
                     help="resident frames to cycle through (0: the workload's sequence length)")
@@ -727,11 +931,13 @@ def main(argv=None):
     if args.precision != "default":
         wl["prec"] = 0 if args.precision == "f32" else 1
         wl["name"] += f" [state overridden: {args.precision}]"
-    if args.cams_per_res and wl.get("pool"):
+    if args.cams_per_res and (wl.get("pool") or wl.get("serve")):
         wl["cams_per_res"] = args.cams_per_res
         wl["name"] += f" [{args.cams_per_res} cameras per resolution]"
     if args.impl == "reference":
         return run_reference(args, wl)
+    if wl.get("serve"):
+        return run_serving(args, wl)
     if wl.get("pool"):
         return run_pool(args, wl)
     return run_gmm(args, wl)

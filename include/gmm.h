@@ -321,6 +321,74 @@ size_t gmm_pool_state_used(const gmm_pool_t *p);
 int gmm_pool_sync(gmm_pool_t *p);
 int gmm_pool_destroy(gmm_pool_t *p);
 
+/* ---------------------------------------------------------------- serving */
+/* Frames from many cameras arriving in host memory at their own pace (the
+ * paper's per-sensor frame stream, §IV, Fig. 4(a), for several sensors as in
+ * §VI), served with continuous batching: an engine thread repeatedly forms a
+ * tick from every camera that has a queued frame and no frame in flight,
+ * uploads those frames, advances them together with one pooled launch,
+ * downloads their masks, and records each frame's latency from its arrival
+ * time to its mask being in host memory. Frames that arrive while a tick is
+ * on the GPU join a later tick; uploads, compute and downloads of
+ * consecutive ticks overlap on separate streams. Each camera's model stays
+ * resident in device memory between its frames. */
+typedef struct gmm_server gmm_server_t;
+
+typedef struct gmm_server_stats {
+    long long pushed, completed, dropped; /* frames */
+    long long admitted, rejected, released; /* camera sessions */
+    long long ticks;                      /* pooled launches */
+    long long pixels;                     /* pixels of completed frames */
+    int live_cams;
+    size_t budget_bytes, used_bytes;      /* state + staging of admitted cameras */
+} gmm_server_stats;
+
+/* budget_bytes caps the device memory of admitted cameras (state plus the
+ * per-camera upload and mask buffers; 0 = no cap). max_cams: slots.
+ * queue_depth: frames a camera may have waiting (>= 1). Starts the engine
+ * thread on the current device. NULL on error. */
+gmm_server_t *gmm_server_create(size_t budget_bytes, int precision, int max_cams,
+                                int queue_depth);
+
+/* Admit a camera (cfg->precision must equal the server's). Returns its id,
+ * or GMM_EBUDGET when its memory would exceed the budget (the admission is
+ * rejected and counted), or another negative status. */
+int gmm_server_admit(gmm_server_t *s, const gmm_config *cfg);
+
+/* End a camera's session: waits (up to timeout_ms; < 0 = no bound) until
+ * its queued frames are done, then frees its slot and memory. */
+int gmm_server_release(gmm_server_t *s, int cam, int timeout_ms);
+
+/* Queue one frame. rgb8_host, depth16_host: host, page-locked for
+ * overlapped copies, read when the frame's tick is formed; mask_host: host,
+ * receives the fused mask. All three must stay valid until the frame is
+ * done. t_arrival: arrival time on the gmm_server_now() clock. Returns a
+ * ticket >= 0, or GMM_EBUDGET if the camera's queue is full (the frame is
+ * dropped and counted), or another negative status. */
+long long gmm_server_push(gmm_server_t *s, int cam, const uint8_t *rgb8_host,
+                          const uint16_t *depth16_host, uint32_t *mask_host,
+                          double t_arrival);
+
+/* 1 if the ticket's mask is in host memory, 0 if not yet, < 0 on error. */
+int gmm_server_done(gmm_server_t *s, long long ticket);
+
+/* Wait (up to timeout_ms; < 0 = no bound) for a ticket. GMM_ETIMEOUT if the
+ * bound ran out. */
+int gmm_server_wait(gmm_server_t *s, long long ticket, int timeout_ms);
+
+/* Counters, and the recorded per-frame latencies in milliseconds (arrival
+ * to mask in host memory, in completion order; copies up to n, returns how
+ * many were recorded in total). */
+int gmm_server_stats_get(gmm_server_t *s, gmm_server_stats *out);
+size_t gmm_server_latencies(gmm_server_t *s, float *ms_out, size_t n);
+
+/* Seconds on the engine's monotonic clock (the clock of t_arrival). */
+double gmm_server_now(void);
+
+/* Stops the engine after the queued frames are done (waits up to
+ * timeout_ms), frees everything. */
+int gmm_server_destroy(gmm_server_t *s, int timeout_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,15 @@ class GMMConfig(ctypes.Structure):
                 ("morph_open", ctypes.c_int)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("pushed", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("dropped", ctypes.c_longlong), ("admitted", ctypes.c_longlong),
+                ("rejected", ctypes.c_longlong), ("released", ctypes.c_longlong),
+                ("ticks", ctypes.c_longlong), ("pixels", ctypes.c_longlong),
+                ("live_cams", ctypes.c_int), ("budget_bytes", ctypes.c_size_t),
+                ("used_bytes", ctypes.c_size_t)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 
@@ -101,6 +110,16 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_pool_state_used": (ctypes.c_size_t, [_vp]),
         "gmm_pool_sync": (ctypes.c_int, [_vp]),
         "gmm_pool_destroy": (ctypes.c_int, [_vp]),
+        "gmm_server_create": (_vp, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "gmm_server_admit": (ctypes.c_int, [_vp, ctypes.POINTER(GMMConfig)]),
+        "gmm_server_release": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+        "gmm_server_push": (ctypes.c_longlong, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double]),
+        "gmm_server_done": (ctypes.c_int, [_vp, ctypes.c_longlong]),
+        "gmm_server_wait": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_int]),
+        "gmm_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
+        "gmm_server_latencies": (ctypes.c_size_t, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+        "gmm_server_now": (ctypes.c_double, []),
+        "gmm_server_destroy": (ctypes.c_int, [_vp, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -370,6 +389,84 @@ class Pool:
         if getattr(self, "_p", None):
             load_library().gmm_pool_destroy(self._p)
             self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching serving engine: cameras join and leave, frames
+    arrive in page-locked host memory, one pooled launch per tick."""
+
+    def __init__(self, budget_bytes=0, precision=PREC_F16, max_cams=256, queue_depth=4,
+                 device=None):
+        import torch
+        L = load_library()
+        self.device = torch.device("cuda" if device is None else device)
+        self.precision = precision
+        with torch.cuda.device(self.device):
+            s = L.gmm_server_create(budget_bytes, precision, max_cams, queue_depth)
+        if not s:
+            raise GMMError(EINVAL, _err())
+        self._s = s
+        self.cams = {}
+
+    @staticmethod
+    def now() -> float:
+        return float(load_library().gmm_server_now())
+
+    def admit(self, H, W, M=3, alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0, init_w=0.05,
+              init_var_d=None, v_min_c=1.0, v_min_d=1.0) -> int:
+        """Camera id; raises GMMError with code EBUDGET when rejected."""
+        L = load_library()
+        cfg = GMMConfig()
+        L.gmm_config_init(ctypes.byref(cfg), H, W, M, alpha, match_k, bg_T, init_var, init_w)
+        if init_var_d is not None:
+            cfg.init_var_d = init_var_d
+        cfg.v_min_c = v_min_c
+        cfg.v_min_d = v_min_d
+        cfg.precision = self.precision
+        cam = _check(L.gmm_server_admit(self._s, ctypes.byref(cfg)))
+        self.cams[cam] = (int(H), int(W), int(M))
+        return cam
+
+    def release(self, cam: int, timeout_ms: int = -1) -> None:
+        _check(load_library().gmm_server_release(self._s, cam, timeout_ms))
+        self.cams.pop(cam, None)
+
+    def push(self, cam, rgb, depth, mask, t_arrival=None) -> int:
+        """Queue a frame (page-locked host tensors or arrays); returns a
+        ticket. Raises GMMError(EBUDGET) when the camera's queue is full."""
+        t = self.now() if t_arrival is None else float(t_arrival)
+        return _check(load_library().gmm_server_push(self._s, cam, _ptr(rgb), _ptr(depth),
+                                                     _ptr(mask), t))
+
+    def done(self, ticket: int) -> bool:
+        return bool(_check(load_library().gmm_server_done(self._s, ticket)))
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> None:
+        _check(load_library().gmm_server_wait(self._s, ticket, timeout_ms))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load_library().gmm_server_stats_get(self._s, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def latencies_ms(self) -> np.ndarray:
+        L = load_library()
+        n = int(L.gmm_server_latencies(self._s, None, 0))
+        out = np.empty(n, dtype=np.float32)
+        if n:
+            L.gmm_server_latencies(self._s, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n)
+        return out
+
+    def close(self, timeout_ms: int = 60000) -> None:
+        if getattr(self, "_s", None):
+            s, self._s = self._s, None
+            _check(load_library().gmm_server_destroy(s, timeout_ms))
 
     def __del__(self):
         try:

@@ -18,7 +18,7 @@ namespace {
 
 // ------------------------------------------------------------ single camera
 template <int M, int PREC>
-__global__ void __launch_bounds__(256, PREC == 0 ? 1 : 4) k_tick(const CamView cv) {
+__device__ __forceinline__ void tick_body(const CamView &cv) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= cv.n_pad) // n_pad is a multiple of 32: whole warps leave
         return;
@@ -26,10 +26,21 @@ __global__ void __launch_bounds__(256, PREC == 0 ? 1 : 4) k_tick(const CamView c
     write_mask_words(cv, p >> 5, bits);
 }
 
+// FP32 state: HBM-bound; the register allocation without a residency hint
+// (64 registers, 4 CTAs per SM) measured fastest. FP16/BF16 state: issue
+// bound; at least 4 CTAs per SM.
+template <int M>
+__global__ void __launch_bounds__(256) k_tick_f32(const CamView cv) { tick_body<M, 0>(cv); }
+template <int M>
+__global__ void __launch_bounds__(256, 4) k_tick_f16(const CamView cv) { tick_body<M, 1>(cv); }
+
 template <int M, int PREC>
 cudaError_t launch_tick_t(const CamView &cv, int threads, cudaStream_t s) {
     const int64_t blocks = (cv.n_pad + threads - 1) / threads;
-    k_tick<M, PREC><<<(unsigned)blocks, threads, 0, s>>>(cv);
+    if (PREC == 0)
+        k_tick_f32<M><<<(unsigned)blocks, threads, 0, s>>>(cv);
+    else
+        k_tick_f16<M><<<(unsigned)blocks, threads, 0, s>>>(cv);
     return cudaGetLastError();
 }
 

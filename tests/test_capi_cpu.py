@@ -113,3 +113,17 @@ def test_mask_pack_roundtrip():
     # bit i of word c is pixel 32c + i, least significant bit first
     m = np.zeros((1, 40), bool); m[0, 0] = True; m[0, 33] = True
     assert G.pack_mask(m).tolist() == [[1, 2]]
+
+
+def test_server_host_checks():
+    L = G.load_library()
+    assert L.gmm_server_create(0, 7, 4, 4) is None
+    assert L.gmm_server_create(0, 0, 0, 4) is None
+    assert L.gmm_server_create(0, 0, 4, 0) is None
+    assert L.gmm_server_admit(None, None) == G.EINVAL
+    assert L.gmm_server_push(None, 0, None, None, None, 0.0) == G.EINVAL
+    assert L.gmm_server_wait(None, 0, 0) == G.EINVAL
+    assert L.gmm_server_destroy(None, 0) == G.EINVAL
+    t0 = L.gmm_server_now()
+    t1 = L.gmm_server_now()
+    assert t1 >= t0 > 0

@@ -1,0 +1,107 @@
+"""The serving engine (continuous batching over the camera pool). Each
+camera's results must be the same alone and in any mix of cameras sharing
+ticks; admission follows the memory budget; full queues drop frames; every
+frame gets a latency."""
+import random
+import time
+
+import numpy as np
+import pytest
+
+import paper_2110_14934_gb300 as G
+from parity import scene_frames, to_dev, words
+
+pytestmark = pytest.mark.gpu
+
+CAMS = [(45, 83, 3), (64, 96, 5), (33, 40, 4), (120, 160, 5), (1, 1, 3), (240, 320, 3)]
+
+
+def _pinned(frames):
+    import torch
+    rgb, depth, _ = frames
+    r = torch.from_numpy(np.ascontiguousarray(rgb)).pin_memory()
+    d = torch.from_numpy(np.ascontiguousarray(depth).view(np.int16)).pin_memory()
+    return r, d
+
+
+@pytest.mark.parametrize("prec", [G.PREC_F16, G.PREC_F32])
+def test_server_results_equal_alone_in_a_changing_mix(prec):
+    import torch
+    n = 10
+    frames = [scene_frames(700 + i, H, W, 1, 40, n) for i, (H, W, M) in enumerate(CAMS)]
+    alone = {}
+    for i, (H, W, M) in enumerate(CAMS):
+        g = G.GMM(H, W, M, precision=prec)
+        for t in range(n):
+            r, d = to_dev(frames[i][0][t], frames[i][1][t])
+            alone[(i, t)] = words(g.apply(r, d)).copy()
+    srv = G.Server(precision=prec, max_cams=8, queue_depth=n)
+    ids = [srv.admit(H, W, M) for (H, W, M) in CAMS]
+    pinned = [_pinned(f) for f in frames]
+    masks = {(i, t): torch.zeros((H, G.mask_words_per_row(W)), dtype=torch.int32).pin_memory()
+             for i, (H, W, M) in enumerate(CAMS) for t in range(n)}
+    order = [(i, t) for t in range(n) for i in range(len(CAMS))]
+    rng = random.Random(4)
+    # frames of a camera stay in order; cameras interleave irregularly, with
+    # pauses so that ticks see different subsets of cameras
+    pos = [0] * len(CAMS)
+    tickets = []
+    while any(p < n for p in pos):
+        i = rng.choice([k for k in range(len(CAMS)) if pos[k] < n])
+        t = pos[i]
+        tickets.append(srv.push(ids[i], pinned[i][0][t], pinned[i][1][t], masks[(i, t)]))
+        pos[i] += 1
+        if rng.random() < 0.2:
+            time.sleep(rng.choice([0.0, 0.0005, 0.002]))
+    for tk in tickets:
+        srv.wait(tk, 30000)
+    for key in alone:
+        assert np.array_equal(masks[key].numpy().view(np.uint32), alone[key]), key
+    st = srv.stats()
+    assert st["completed"] == len(order) and st["dropped"] == 0 and st["ticks"] >= n
+    lat = srv.latencies_ms()
+    assert lat.size == len(order) and np.all(lat > 0) and np.all(lat < 30000)
+    srv.close()
+
+
+def test_server_budget_admission_and_release():
+    per = G.state_bytes(120, 160, 5, G.PREC_F16)
+    srv = G.Server(budget_bytes=int(2.5 * per) + 400000, precision=G.PREC_F16, max_cams=4)
+    a = srv.admit(120, 160, 5)
+    b = srv.admit(120, 160, 5)
+    with pytest.raises(G.GMMError) as e:
+        srv.admit(120, 160, 5)
+    assert e.value.code == G.EBUDGET
+    st = srv.stats()
+    assert st["admitted"] == 2 and st["rejected"] == 1 and st["live_cams"] == 2
+    srv.release(a, 10000)
+    c = srv.admit(120, 160, 5)
+    st = srv.stats()
+    assert st["admitted"] == 3 and st["released"] == 1 and st["live_cams"] == 2
+    srv.release(b, 10000)
+    srv.release(c, 10000)
+    assert srv.stats()["used_bytes"] == 0
+    srv.close()
+
+
+def test_server_full_queue_drops_frames():
+    import torch
+    H, W, M = 720, 1280, 5
+    rgb, depth = _pinned(scene_frames(3, H, W, 1, 0, 2))
+    srv = G.Server(precision=G.PREC_F16, max_cams=2, queue_depth=1)
+    cam = srv.admit(H, W, M)
+    mask = torch.zeros((H, G.mask_words_per_row(W)), dtype=torch.int32).pin_memory()
+    tickets, drops = [], 0
+    for k in range(40):
+        try:
+            tickets.append(srv.push(cam, rgb[k % 2], depth[k % 2], mask))
+        except G.GMMError as e:
+            assert e.code == G.EBUDGET
+            drops += 1
+    for tk in tickets:
+        srv.wait(tk, 30000)
+    st = srv.stats()
+    assert drops >= 1 and st["dropped"] == drops
+    assert st["pushed"] == len(tickets) and st["completed"] == len(tickets)
+    srv.release(cam, 10000)
+    srv.close()

@@ -215,6 +215,19 @@ int gmm_fuse_masks(const uint32_t *fg_rgb, const uint32_t *fg_d,
 int gmm_morph_open3(const uint32_t *mask_in, uint32_t *mask_out, int H, int W,
                     void *stream);
 
+/* Pack a byte mask (device, H*W bytes row-major, non-zero = foreground) into
+ * the bit-packed mask layout (device). Asynchronous on `stream`. */
+int gmm_pack_mask(const uint8_t *bytes, uint32_t *mask_out, int H, int W,
+                  void *stream);
+
+/* Confusion counts of a predicted mask against a ground-truth mask (both
+ * bit-packed, device), the quantities of the paper's evaluation (§V.A):
+ * recall R = TP/(TP+FN) (Eq. 1), precision P = TP/(TP+FP) (Eq. 2), F1 =
+ * 2PR/(P+R) (Eq. 3). counts_out: device, 4 unsigned 64-bit values
+ * {TP, FP, FN, TN}, overwritten. Asynchronous on `stream`. */
+int gmm_mask_confusion(const uint32_t *pred, const uint32_t *truth, int H, int W,
+                       unsigned long long *counts_out, void *stream);
+
 /* ------------------------------------------------- allocation-free variant */
 /* The paper has no counterpart to this entry point; it exists for callers
  * that must not allocate device memory, such as a host application that

@@ -92,6 +92,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_state_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
         "gmm_fuse_masks": (ctypes.c_int, [_vp] * 4 + [ctypes.c_int, ctypes.c_int, _vp]),
         "gmm_morph_open3": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp]),
+        "gmm_pack_mask": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp]),
+        "gmm_mask_confusion": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
         "gmm_apply_open3_noalloc": (ctypes.c_int, [ctypes.POINTER(GMMConfig), _vp, ctypes.c_int,
                                                    _vp, _vp, _vp, _vp]),
         "gmm_pool_create": (_vp, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
@@ -479,6 +481,33 @@ def fuse_masks(fg_rgb, fg_d, fusion, mask_out, H, W, stream=None) -> None:
     """List 1 alone on bit-packed device masks; fusion bytes updated in place."""
     _check(load_library().gmm_fuse_masks(_ptr(fg_rgb), _ptr(fg_d), _ptr(fusion), _ptr(mask_out),
                                          H, W, _stream_ptr(stream, fusion.device)))
+
+
+def pack_mask_device(byte_mask, H, W, out=None, stream=None):
+    """Byte mask tensor [H, W] (device) -> bit-packed int32 words (device)."""
+    import torch
+    if out is None:
+        out = torch.empty((H, mask_words_per_row(W)), dtype=torch.int32, device=byte_mask.device)
+    _check(load_library().gmm_pack_mask(_ptr(byte_mask), _ptr(out), H, W,
+                                        _stream_ptr(stream, byte_mask.device)))
+    return out
+
+
+def mask_scores(pred, truth, H, W, counts=None, stream=None) -> dict:
+    """TP/FP/FN/TN of bit-packed device masks counted on the GPU, with recall,
+    precision and F1 (Eq. 1-3, §V.A). Synchronises the stream."""
+    import torch
+    if counts is None:
+        counts = torch.empty(4, dtype=torch.int64, device=pred.device)
+    s = torch.cuda.current_stream(pred.device) if stream is None else stream
+    _check(load_library().gmm_mask_confusion(_ptr(pred), _ptr(truth), H, W, _ptr(counts),
+                                             s.cuda_stream))
+    s.synchronize()
+    tp, fp, fn, tn = (int(v) for v in counts.cpu().tolist())
+    R = tp / (tp + fn) if tp + fn else 0.0
+    P = tp / (tp + fp) if tp + fp else 0.0
+    F1 = 2 * P * R / (P + R) if P + R else 0.0
+    return {"tp": tp, "fp": fp, "fn": fn, "tn": tn, "recall": R, "precision": P, "f1": F1}
 
 
 def morph_open3(mask_in, mask_out, H, W, stream=None) -> None:

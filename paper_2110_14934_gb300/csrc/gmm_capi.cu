@@ -661,6 +661,32 @@ int gmm_fuse_masks(const uint32_t *fg_rgb, const uint32_t *fg_d, uint8_t *fusion
     return e == cudaSuccess ? GMM_OK : cuda_fail(nullptr, e, "gmm_fuse_masks");
 }
 
+int gmm_pack_mask(const uint8_t *bytes, uint32_t *mask_out, int H, int W, void *stream) {
+    if (H < 1 || W < 1)
+        return fail(GMM_EINVAL, "gmm_pack_mask: H and W must be >= 1");
+    if (!bytes || !mask_out || reinterpret_cast<uintptr_t>(mask_out) % 4)
+        return fail(GMM_EINVAL, "gmm_pack_mask: null or misaligned pointer");
+    if (!device_accessible(bytes) || !device_accessible(mask_out))
+        return fail(GMM_EINVAL, "gmm_pack_mask: pointers must be device-accessible");
+    const cudaError_t e = gmmhost::launch_pack(bytes, mask_out, H, W,
+                                               static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GMM_OK : cuda_fail(nullptr, e, "gmm_pack_mask");
+}
+
+int gmm_mask_confusion(const uint32_t *pred, const uint32_t *truth, int H, int W,
+                       unsigned long long *counts_out, void *stream) {
+    if (H < 1 || W < 1)
+        return fail(GMM_EINVAL, "gmm_mask_confusion: H and W must be >= 1");
+    if (!pred || !truth || !counts_out || reinterpret_cast<uintptr_t>(pred) % 4 ||
+        reinterpret_cast<uintptr_t>(truth) % 4 || reinterpret_cast<uintptr_t>(counts_out) % 8)
+        return fail(GMM_EINVAL, "gmm_mask_confusion: null or misaligned pointer");
+    if (!device_accessible(pred) || !device_accessible(truth) || !device_accessible(counts_out))
+        return fail(GMM_EINVAL, "gmm_mask_confusion: pointers must be device-accessible");
+    const cudaError_t e = gmmhost::launch_confusion(pred, truth, H, W, counts_out,
+                                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GMM_OK : cuda_fail(nullptr, e, "gmm_mask_confusion");
+}
+
 int gmm_morph_open3(const uint32_t *mask_in, uint32_t *mask_out, int H, int W, void *stream) {
     if (H < 1 || W < 1)
         return fail(GMM_EINVAL, "gmm_morph_open3: H and W must be >= 1");

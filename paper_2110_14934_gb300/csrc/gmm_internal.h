@@ -18,6 +18,12 @@ cudaError_t launch_tick(const gmmdev::CamView &cv, int threads, cudaStream_t s);
 cudaError_t launch_tick_staged(const gmmdev::CamView &cv, int variant, int ctas_per_sm,
                                int *status, cudaStream_t s);
 
+// Byte mask -> bit-packed mask; confusion counts {TP, FP, FN, TN} of two
+// bit-packed masks into out (zeroed first).
+cudaError_t launch_pack(const uint8_t *in, uint32_t *out, int H, int W, cudaStream_t s);
+cudaError_t launch_confusion(const uint32_t *pred, const uint32_t *truth, int H, int W,
+                             unsigned long long *out, cudaStream_t s);
+
 // List 1 alone over bit-packed inputs.
 cudaError_t launch_fuse(const uint32_t *fg_rgb, const uint32_t *fg_d, uint8_t *fusion,
                         uint32_t *mask, int H, int W, cudaStream_t s);

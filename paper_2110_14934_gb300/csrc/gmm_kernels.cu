@@ -190,6 +190,57 @@ __global__ void __launch_bounds__(kMR * kMW) k_morph_open3(const uint32_t *in, u
     }
 }
 
+// ------------------------------------------------------------ mask metrics
+// Byte mask (H*W, non-zero = 1) to the bit-packed layout: one thread per
+// padded pixel, one ballot per word.
+__global__ void __launch_bounds__(256) k_pack(const uint8_t *in, uint32_t *out, int H, int W,
+                                              int wpr) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)H * wpr * 32)
+        return;
+    const int64_t row = (p >> 5) / wpr;
+    const int x = (int)(p - row * wpr * 32);
+    const uint32_t b = (x < W && in[row * W + x] != 0) ? 1u : 0u;
+    const uint32_t word = __ballot_sync(0xffffffffu, b);
+    if ((p & 31) == 0)
+        out[p >> 5] = word;
+}
+
+// Confusion counts of a predicted mask against a truth mask (both
+// bit-packed, bits beyond W ignored): out = {TP, FP, FN, TN}, accumulated.
+__global__ void __launch_bounds__(256) k_confusion(const uint32_t *pred, const uint32_t *truth,
+                                                   int H, int W, int wpr,
+                                                   unsigned long long *out) {
+    unsigned long long c[4] = {0, 0, 0, 0}; // TP, FP, FN, TN
+    const int64_t n_words = (int64_t)H * wpr;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_words;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int col = (int)(i % wpr);
+        const int rem = W - 32 * col;
+        const uint32_t valid = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+        const uint32_t p = pred[i], t = truth[i];
+        c[0] += __popc(p & t & valid);
+        c[1] += __popc(p & ~t & valid);
+        c[2] += __popc(~p & t & valid);
+        c[3] += __popc(~p & ~t & valid);
+    }
+    __shared__ unsigned long long s[4][8]; // blockDim.x = 256: 8 warps
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        for (int off = 16; off > 0; off >>= 1)
+            c[k] += __shfl_xor_sync(0xffffffffu, c[k], off);
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 4; ++k)
+            s[k][threadIdx.x >> 5] = c[k];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        unsigned long long v = 0;
+        for (int w = 0; w < 8; ++w)
+            v += s[threadIdx.x][w];
+        atomicAdd(&out[threadIdx.x], v);
+    }
+}
+
 } // namespace
 
 namespace gmmhost {
@@ -236,6 +287,30 @@ cudaError_t launch_pool_tick_impl(const PoolArgs &a, int threads, int blocks, in
         k_pool_tick<0><<<blocks, threads, 0, s>>>(a);
     else
         k_pool_tick<1><<<blocks, threads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const uint8_t *in, uint32_t *out, int H, int W, cudaStream_t s) {
+    const int wpr = (W + 31) / 32;
+    const int64_t n = (int64_t)H * wpr * 32;
+    if (n == 0)
+        return cudaSuccess;
+    k_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, H, W, wpr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_confusion(const uint32_t *pred, const uint32_t *truth, int H, int W,
+                             unsigned long long *out, cudaStream_t s) {
+    const int wpr = (W + 31) / 32;
+    const int64_t n_words = (int64_t)H * wpr;
+    cudaError_t e = cudaMemsetAsync(out, 0, 4 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n_words == 0)
+        return e;
+    int64_t blocks = (n_words + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    if (blocks > cap)
+        blocks = cap;
+    k_confusion<<<(unsigned)blocks, 256, 0, s>>>(pred, truth, H, W, wpr, out);
     return cudaGetLastError();
 }
 

@@ -29,8 +29,10 @@ _lock = threading.Lock()
 _lib = None
 
 # Parameter vector layout of gmm_oracle.c.
-P_ALPHA, P_K, P_T, P_INIT_VAR, P_INIT_W, P_VMIN, P_EPS = range(7)
+P_ALPHA, P_K, P_T, P_INIT_VAR, P_INIT_W, P_VMIN, P_EPS, P_FLAGS = range(8)
 NEAR_MATCH, NEAR_T, NEAR_KEY = 1, 2, 4
+FLAG_RHO_ETA, FLAG_VAR_PER_CHANNEL = 1, 2
+DEPTH_SCALE_DEFAULT = 255.0 / 4095.0
 
 # Plane order of the product library's state (gmm.h, GMM_PLANE_*); used only
 # to lay the oracle's pixel-major state out the same way for comparison.
@@ -85,7 +87,10 @@ def _declare(L):
     L.oracle_tick.restype = None
     L.oracle_morph_open3.argtypes = [ctypes.c_int, ctypes.c_int, _u8p, _u8p, _u8p]
     L.oracle_morph_open3.restype = None
-    assert L.oracle_param_count() == 7
+    L.oracle_tick_augmented.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                        ctypes.c_int, _dp, _dp, _dp, _u8p, _u16p, _u8p, _u8p]
+    L.oracle_tick_augmented.restype = None
+    assert L.oracle_param_count() == 8
 
 
 def _ptr(a: np.ndarray, ctype):
@@ -98,10 +103,10 @@ def f32(x: float) -> float:
     return float(np.float32(x))
 
 
-def stream_params(alpha, k, T, init_var, init_w, v_min=1.0, eps=1e-5) -> np.ndarray:
+def stream_params(alpha, k, T, init_var, init_w, v_min=1.0, eps=1e-5, flags=0) -> np.ndarray:
     """Parameter vector; every value is the float32 value the product library sees."""
-    return np.array([f32(alpha), f32(k), f32(T), f32(init_var), f32(init_w), f32(v_min), eps],
-                    dtype=np.float64)
+    return np.array([f32(alpha), f32(k), f32(T), f32(init_var), f32(init_w), f32(v_min), eps,
+                     float(flags)], dtype=np.float64)
 
 
 # ----------------------------------------------------------------- pixel level
@@ -163,14 +168,14 @@ class OracleGMM:
     because the product library receives them as floats."""
 
     def __init__(self, H, W, M, alpha, match_k, bg_T, init_var, init_w,
-                 init_var_d=None, v_min_c=1.0, v_min_d=1.0, eps=1e-5):
+                 init_var_d=None, v_min_c=1.0, v_min_d=1.0, eps=1e-5, flags=0):
         if not (3 <= M <= 5):
             raise ValueError("M must be in [3, 5]")
         self.H, self.W, self.M = int(H), int(W), int(M)
         N = self.H * self.W
         iv_d = init_var if init_var_d is None else init_var_d
-        self.prm_c = stream_params(alpha, match_k, bg_T, init_var, init_w, v_min_c, eps)
-        self.prm_d = stream_params(alpha, match_k, bg_T, iv_d, init_w, v_min_d, eps)
+        self.prm_c = stream_params(alpha, match_k, bg_T, init_var, init_w, v_min_c, eps, flags)
+        self.prm_d = stream_params(alpha, match_k, bg_T, iv_d, init_w, v_min_d, eps, flags)
         self.wc = np.zeros((N, M)); self.muc = np.zeros((N, M, 3)); self.vc = np.zeros((N, M))
         self.wd = np.zeros((N, M)); self.mud = np.zeros((N, M)); self.vd = np.zeros((N, M))
         self.F = np.zeros(N, dtype=np.int8); self.cpt = np.zeros(N, dtype=np.int8)
@@ -237,6 +242,56 @@ class OracleGMM:
         self.F[:] = (f & 1).astype(np.int8)
         self.cpt[:] = (((f >> 1) & 7) - 3).astype(np.int8)
         self.dinit[:] = ((f >> 4) & 1).astype(np.uint8)
+        self.first = False
+
+
+class OracleAugmented:
+    """The augmentation alternative (§III.B): one mixture per pixel over R, G,
+    B and depth * depth_scale; one foreground bit per pixel, no fusion."""
+
+    def __init__(self, H, W, M, alpha, match_k, bg_T, init_var, init_w, v_min=1.0, eps=1e-5,
+                 flags=0, depth_scale=DEPTH_SCALE_DEFAULT):
+        self.H, self.W, self.M = int(H), int(W), int(M)
+        N = self.H * self.W
+        self.prm = stream_params(alpha, match_k, bg_T, init_var, init_w, v_min, eps, flags)
+        self.depth_scale = f32(depth_scale)
+        self.w = np.zeros((N, M)); self.mu = np.zeros((N, M, 4)); self.v = np.zeros((N, M))
+        self.first = True
+
+    def tick(self, rgb, depth) -> dict:
+        H, W = self.H, self.W
+        rgb = np.ascontiguousarray(rgb, dtype=np.uint8).reshape(H, W, 3)
+        depth = np.ascontiguousarray(depth, dtype=np.uint16).reshape(H, W)
+        fg = np.zeros(H * W, np.uint8); near = np.zeros(H * W, np.uint8)
+        d = ctypes.c_double
+        lib().oracle_tick_augmented(H, W, self.M, _ptr(self.prm, d), self.depth_scale, int(self.first),
+                                    _ptr(self.w, d), _ptr(self.mu, d), _ptr(self.v, d),
+                                    _ptr(rgb, ctypes.c_uint8), _ptr(depth, ctypes.c_uint16),
+                                    _ptr(fg, ctypes.c_uint8), _ptr(near, ctypes.c_uint8))
+        self.first = False
+        return {"fg": fg.reshape(H, W), "near": near.reshape(H, W)}
+
+    def planes(self) -> np.ndarray:
+        """State in the library's plane layout for this mode: [M, 8, H, W] with
+        w in plane 0, the R, G, B means in planes 1-3, v in plane 4 and the
+        depth-channel mean in plane 6 (planes 5 and 7 unused, zero)."""
+        H, W, M = self.H, self.W, self.M
+        out = np.zeros((M, 8, H, W))
+        out[:, 0] = self.w.T.reshape(M, H, W)
+        for c in range(3):
+            out[:, 1 + c] = self.mu[:, :, c].T.reshape(M, H, W)
+        out[:, 4] = self.v.T.reshape(M, H, W)
+        out[:, 6] = self.mu[:, :, 3].T.reshape(M, H, W)
+        return out
+
+    def set_state(self, planes: np.ndarray) -> None:
+        H, W, M = self.H, self.W, self.M
+        p = np.asarray(planes, dtype=np.float64).reshape(M, 8, H * W)
+        self.w[:] = p[:, 0].T
+        for c in range(3):
+            self.mu[:, :, c] = p[:, 1 + c].T
+        self.v[:] = p[:, 4].T
+        self.mu[:, :, 3] = p[:, 6].T
         self.first = False
 
 

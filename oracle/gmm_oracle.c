@@ -37,6 +37,17 @@
  *     the depth foreground copies the colour one;
  *   - fusion follows List 1 literally, with both label and counter starting
  *     at zero.
+ * Options (bits of the stream's flags parameter), each another reading:
+ *   - RHO_ETA: the matched component's mean and variance move with
+ *     rho = alpha * eta(x | mu, sigma), eta the isotropic Gaussian density at
+ *     the sample with the component's parameters before the update
+ *     (Stauffer-Grimson's second learning rate), capped at 1;
+ *   - VAR_PER_CHANNEL: v tracks the squared distance divided by the number of
+ *     channels (the per-channel variance sigma^2), so the match test
+ *     d^2 < k^2 v is the Mahalanobis test with covariance sigma^2 I; without
+ *     it v tracks the summed squared distance and sigma^2 = v / D.
+ * The augmentation alternative of §III.B (one mixture over R, G, B and the
+ * depth brought to the byte range) is oracle_tick_augmented below.
  *
  * Near-threshold report. For each stream step the oracle also reports, in its
  * own arithmetic, whether any decision sat within a relative distance `eps` of
@@ -45,6 +56,7 @@
  * (bit 2). A lower-precision implementation may legitimately decide those
  * cases the other way.
  */
+
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -52,10 +64,12 @@
 #define ORACLE_MAX_M 5
 
 enum { NEAR_MATCH = 1, NEAR_T = 2, NEAR_KEY = 4 };
+enum { FLAG_RHO_ETA = 1, FLAG_VAR_PER_CHANNEL = 2 };
+static const double kPi = 3.14159265358979323846;
 
 /* Stream parameters, in this order (a plain double array keeps the ABI
- * trivial): alpha, k, T, init_var, init_w, v_min, eps. */
-enum { P_ALPHA, P_K, P_T, P_INIT_VAR, P_INIT_W, P_VMIN, P_EPS, P_COUNT };
+ * trivial): alpha, k, T, init_var, init_w, v_min, eps, flags. */
+enum { P_ALPHA, P_K, P_T, P_INIT_VAR, P_INIT_W, P_VMIN, P_EPS, P_FLAGS, P_COUNT };
 
 int oracle_param_count(void) { return P_COUNT; }
 
@@ -126,6 +140,7 @@ int oracle_stream_step(int M, int D, const double *prm, double *w, double *mu,
     const double alpha = prm[P_ALPHA], k = prm[P_K], T = prm[P_T];
     const double init_var = prm[P_INIT_VAR], init_w = prm[P_INIT_W];
     const double v_min = prm[P_VMIN], eps = prm[P_EPS];
+    const int flags = (int)prm[P_FLAGS];
     int near = 0;
 
     /* 1. Match: distance of the sample to each mean, tested from the best
@@ -168,16 +183,32 @@ int oracle_stream_step(int M, int D, const double *prm, double *w, double *mu,
         w[i] = w[i] / s;
 
     /* 3. Matched component: mean and variance move toward the sample with
-     *    rate alpha; the variance uses the updated mean. */
+     *    rate rho (alpha, or alpha * eta with RHO_ETA); the variance uses the
+     *    updated mean. */
     if (matched) {
+        double rho = alpha;
+        if (flags & FLAG_RHO_ETA) {
+            const double s2 = (flags & FLAG_VAR_PER_CHANNEL) ? v[j] : v[j] / D;
+            double d2 = 0.0;
+            for (int c = 0; c < D; c++) {
+                double diff = x[c] - mu[j * D + c];
+                d2 += diff * diff;
+            }
+            const double eta = pow(2.0 * kPi * s2, -0.5 * D) * exp(-d2 / (2.0 * s2));
+            rho = alpha * eta;
+            if (rho > 1.0)
+                rho = 1.0;
+        }
         for (int c = 0; c < D; c++)
-            mu[j * D + c] = (1.0 - alpha) * mu[j * D + c] + alpha * x[c];
+            mu[j * D + c] = (1.0 - rho) * mu[j * D + c] + rho * x[c];
         double d2 = 0.0;
         for (int c = 0; c < D; c++) {
             double diff = x[c] - mu[j * D + c];
             d2 += diff * diff;
         }
-        double vn = (1.0 - alpha) * v[j] + alpha * d2;
+        if (flags & FLAG_VAR_PER_CHANNEL)
+            d2 = d2 / D;
+        double vn = (1.0 - rho) * v[j] + rho * d2;
         v[j] = vn < v_min ? v_min : vn;
     }
 
@@ -191,7 +222,7 @@ int oracle_stream_step(int M, int D, const double *prm, double *w, double *mu,
                 near |= NEAR_KEY;
         }
     }
-    double tw[ORACLE_MAX_M], tmu[ORACLE_MAX_M * 3], tv[ORACLE_MAX_M];
+    double tw[ORACLE_MAX_M], tmu[ORACLE_MAX_M * 4], tv[ORACLE_MAX_M];
     int rank_j = -1;
     for (int r = 0; r < M; r++) {
         int p = perm[r];
@@ -309,6 +340,40 @@ void oracle_tick(int H, int W, int M, const double *prm_c, const double *prm_d,
             fused[n] = (uint8_t)Fi;
         if (near)
             near[n] = (uint8_t)nbits;
+    }
+}
+
+/* The augmentation alternative (§III.B, Fig. 2): one mixture over four
+ * channels, R, G, B and the depth reading times depth_scale (bringing
+ * millimetres to the byte range of the colour channels). A zero depth reading
+ * takes the depth mean of the best-ranked component (the value the model
+ * expects, so the fourth channel neither adds distance nor moves), or 0 on
+ * the first frame. State pixel-major: w[N*M], mu[N*M*4], v[N*M]. Output: the
+ * foreground bit per pixel (no fusion); near as in oracle_tick. */
+void oracle_tick_augmented(int H, int W, int M, const double *prm, double depth_scale,
+                           int first, double *w, double *mu, double *v,
+                           const uint8_t *rgb, const uint16_t *depth, uint8_t *fg,
+                           uint8_t *near)
+{
+    const long N = (long)H * (long)W;
+    for (long n = 0; n < N; n++) {
+        double *wn = w + n * M, *mn = mu + n * M * 4, *vn = v + n * M;
+        double x[4] = {(double)rgb[3 * n], (double)rgb[3 * n + 1], (double)rgb[3 * n + 2],
+                       depth_scale * (double)depth[n]};
+        if (depth[n] == 0)
+            x[3] = first ? 0.0 : mn[3];
+        int f = 0, nb = 0;
+        if (first) {
+            oracle_stream_init(M, 4, prm[P_INIT_VAR], wn, mn, vn, x);
+        } else {
+            int info[4];
+            f = oracle_stream_step(M, 4, prm, wn, mn, vn, x, info);
+            nb = info[3];
+        }
+        if (fg)
+            fg[n] = (uint8_t)f;
+        if (near)
+            near[n] = (uint8_t)nb;
     }
 }
 

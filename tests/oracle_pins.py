@@ -329,10 +329,101 @@ def check_depth_invalid_and_late_start():
     assert np.allclose(g.mud[0], 1500.0) and np.allclose(g.wd[0], 1 / 3)
 
 
+def check_closed_form_per_channel_variance():
+    """With VAR_PER_CHANNEL the variance tracks |x - mu|^2 / D, so under a
+    constant input v_t = r^t [v_0 + |mu_0 - c|^2 / D * r (1 - r^t)]."""
+    alpha = 0.03125
+    r = 1.0 - alpha
+    for D, c, mu0 in ((3, np.array([80.0, 90.0, 100.0]), np.array([84.0, 87.0, 101.0])),
+                      (1, np.array([1500.0]), np.array([1497.0]))):
+        e = float(np.sum((mu0 - c) ** 2))
+        prm = O.stream_params(alpha, 2.5, 0.7, 900.0, 0.05, v_min=1e-3,
+                              flags=O.FLAG_VAR_PER_CHANNEL)
+        w = np.array([0.7, 0.2, 0.1]); mu = np.zeros((3, D)); mu[0] = mu0
+        mu[1] = c + 400.0; mu[2] = c + 900.0
+        v = np.array([30.0, 500.0, 800.0])
+        for t in range(1, 120):
+            fg, info = O.stream_step(prm, w, mu, v, c)
+            assert info[0] == 0 and info[2] == 0 and fg == 0
+            rt = r ** t
+            assert np.isclose(v[0], rt * (30.0 + e / D * r * (1.0 - rt)), rtol=1e-11), (D, t)
+            assert np.allclose(mu[0], c + (mu0 - c) * rt, rtol=1e-12, atol=1e-10)
+
+
+def check_rho_eta_against_scipy():
+    """RHO_ETA: the matched component moves with rho = alpha * N(x; mu,
+    sigma^2 I), the density taken from scipy, with sigma^2 = v / D by default
+    and v under VAR_PER_CHANNEL."""
+    from scipy.stats import multivariate_normal
+    alpha = 0.25
+    for D in (1, 3):
+        for flags in (O.FLAG_RHO_ETA, O.FLAG_RHO_ETA | O.FLAG_VAR_PER_CHANNEL):
+            mu0 = np.array([100.0, 50.0, 75.0][:D]); x = mu0 + np.array([1.5, -2.0, 0.5][:D])
+            v0 = 6.0
+            s2 = v0 if flags & O.FLAG_VAR_PER_CHANNEL else v0 / D
+            rho = alpha * multivariate_normal.pdf(x, mean=mu0, cov=s2 * np.eye(D))
+            prm = O.stream_params(alpha, 3.0, 0.7, 400.0, 0.05, v_min=1e-3, flags=flags)
+            w = np.array([0.8, 0.15, 0.05]); mu = np.zeros((3, D)); mu[0] = mu0
+            mu[1] = mu0 + 300.0; mu[2] = mu0 + 600.0
+            v = np.array([v0, 400.0, 400.0])
+            fg, info = O.stream_step(prm, w, mu, v, x)
+            assert info[0] == 0 and info[2] == 0
+            mu_new = (1 - rho) * mu0 + rho * x
+            d2 = float(np.sum((x - mu_new) ** 2))
+            if flags & O.FLAG_VAR_PER_CHANNEL:
+                d2 /= D
+            assert np.allclose(mu[0], mu_new, rtol=1e-13), (D, flags)
+            assert np.isclose(v[0], (1 - rho) * v0 + rho * d2, rtol=1e-12), (D, flags)
+
+
+def check_augmented_model():
+    """The augmentation alternative: depth enters as a fourth channel scaled
+    to the byte range; a zero reading takes the best-ranked component's depth
+    mean, which is the same as feeding that value explicitly."""
+    s = np.float32(255.0 / 4095.0)
+    g = O.OracleAugmented(1, 2, 4, 0.05, 2.5, 0.7, 100.0, 0.05)
+    rgb = np.array([[[90, 100, 110], [30, 40, 50]]], np.uint8)
+    g.tick(rgb, np.array([[2000, 3000]], np.uint16))
+    assert np.allclose(g.mu[0, :, 3], float(s) * 2000.0) and np.allclose(g.mu[1, :, 3], float(s) * 3000.0)
+    # distinct components, in rank order, so that the imputed value is specific
+    planes = g.planes()
+    planes[:, 6, 0, 1] = [186.0, 170.0, 205.0, 150.0]   # depth-channel means
+    planes[:, 0, 0, 1] = [0.55, 0.25, 0.15, 0.05]
+    planes[:, 4, 0, 1] = [30.0, 60.0, 90.0, 120.0]
+    g.set_state(planes)
+    ref_w, ref_mu, ref_v = g.w[1].copy(), g.mu[1].copy(), g.v[1].copy()
+    rgb2 = rgb.copy(); rgb2[0, 1] = (33, 38, 52)
+    g.tick(rgb2, np.array([[2004, 0]], np.uint16))
+    # the same step through the generic four-channel update with the imputed value
+    prm = O.stream_params(0.05, 2.5, 0.7, 100.0, 0.05)
+    x = np.array([33.0, 38.0, 52.0, ref_mu[0, 3]])
+    O.stream_step(prm, ref_w, ref_mu, ref_v, x)
+    assert np.array_equal(g.w[1], ref_w) and np.array_equal(g.mu[1], ref_mu)
+    assert np.array_equal(g.v[1], ref_v)
+    # Depth is one channel of four (§III.B, Fig. 2): with colour noise of
+    # sigma 3 per channel the summed variance settles near 27, so a 150 mm
+    # depth step at unchanged colour adds (150 s)^2 = 87 < k^2 v to the squared
+    # distance and the augmented model misses it; the separate depth model
+    # (sigma 5 mm) flags it.
+    rng = np.random.default_rng(1)
+    h = O.OracleAugmented(1, 1, 3, 0.05, 2.5, 0.7, 100.0, 0.05)
+    sep = O.OracleGMM(1, 1, 3, 0.05, 2.5, 0.7, 100.0, 0.05)
+    for t in range(80):
+        c = np.clip(np.round(120 + rng.normal(0, 3, 3)), 0, 255).astype(np.uint8).reshape(1, 1, 3)
+        d = np.array([[int(round(2500 + rng.normal(0, 5)))]], np.uint16)
+        h.tick(c, d)
+        sep.tick(c, d)
+    c = np.full((1, 1, 3), 120, np.uint8)
+    d = np.array([[2350]], np.uint16)
+    assert h.tick(c, d)["fg"][0, 0] == 0
+    assert sep.tick(c, d)["fg_d"][0, 0] == 1
+
+
 ALL_CHECKS = [
     check_hand_trace, check_list1_traces, check_list1_properties,
     check_closed_form_constant_input, check_closed_form_depth,
     check_invariants_random, check_special_case_T_near_one, check_first_match_wins,
     check_rank_order_bruteforce, check_background_count_exact,
     check_morph_open_against_scipy, check_depth_invalid_and_late_start,
+    check_closed_form_per_channel_variance, check_rho_eta_against_scipy, check_augmented_model,
 ]

@@ -27,15 +27,27 @@ MUTANTS = {
     "payload_not_permuted": ("tmu[r * D + c] = mu[p * D + c];", "tmu[r * D + c] = mu[r * D + c];"),
     "B_not_strict": ("if (s > T)", "if (s >= T)"),
     "fg_rank_off_by_one": ("(rank_j >= B)", "(rank_j > B)"),
-    "variance_old_mean": ("double diff = x[c] - mu[j * D + c];",
-                          "double diff = (x[c] - mu[j * D + c]) / (1.0 - alpha);"),
-    "variance_no_decay": ("double vn = (1.0 - alpha) * v[j] + alpha * d2;", "double vn = v[j] + alpha * d2;"),
+    "variance_old_mean": ("            double diff = x[c] - mu[j * D + c];\n            d2 += diff * diff;\n"
+                          "        }\n        if (flags",
+                          "            double diff = (x[c] - mu[j * D + c]) / (1.0 - rho);\n"
+                          "            d2 += diff * diff;\n        }\n        if (flags"),
+    "variance_no_decay": ("double vn = (1.0 - rho) * v[j] + rho * d2;", "double vn = v[j] + rho * d2;"),
+    "mean_rate_fixed_alpha": ("mu[j * D + c] = (1.0 - rho) * mu[j * D + c] + rho * x[c];",
+                              "mu[j * D + c] = (1.0 - alpha) * mu[j * D + c] + alpha * x[c];"),
     "init_weight_unnormalised": ("w[i] = 1.0 / (double)M;", "w[i] = 1.0;"),
     "list1_three_frames": ("if (*cpt == 3)", "if (*cpt == 2)"),
     "list1_plus3_to_depth": ("*F = f_rgb;", "*F = f_d;"),
     "list1_counter_direction": ("*cpt = *cpt + 1;", "*cpt = *cpt - 1;"),
     "invalid_depth_background": ("fdp = fc;", "fdp = 0;"),
     "morph_outside_one": ("int val = 0;", "int val = 1;"),
+    "eta_power": ("pow(2.0 * kPi * s2, -0.5 * D)", "pow(2.0 * kPi * s2, -1.0 * D)"),
+    "eta_exponent_halving": ("exp(-d2 / (2.0 * s2))", "exp(-d2 / s2)"),
+    "eta_sigma_swapped": ("(flags & FLAG_VAR_PER_CHANNEL) ? v[j] : v[j] / D",
+                          "(flags & FLAG_VAR_PER_CHANNEL) ? v[j] / D : v[j]"),
+    "per_channel_no_divide": ("d2 = d2 / D;", "d2 = d2;"),
+    "augmented_imputes_wrong_component": ("x[3] = first ? 0.0 : mn[3];",
+                                          "x[3] = first ? 0.0 : mn[7];"),
+    "augmented_depth_unscaled": ("depth_scale * (double)depth[n]};", "(double)depth[n]};"),
 }
 
 
@@ -55,7 +67,7 @@ def swap_oracle_lib():
 def test_pins_catch_mutant(name, tmp_path, swap_oracle_lib):
     old, new = MUTANTS[name]
     src = open(SRC).read()
-    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    assert src.count(old) == 1, f"mutation site for {name} not found or not unique"
     mutated = src.replace(old, new, 1)
     c_path = tmp_path / "mutant.c"
     c_path.write_text(mutated)

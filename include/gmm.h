@@ -99,7 +99,37 @@ typedef struct gmm_config {
     float v_min_d;     /* depth variance floor, > 0; default 1 */
     int precision;     /* GMM_PREC_F32 (default) or GMM_PREC_F16 */
     int morph_open;    /* 1: mask_out gets a 3x3 opening of the fused mask */
+    int mode;          /* GMM_MODE_FUSION (default) or GMM_MODE_AUGMENTED */
+    float depth_scale; /* GMM_MODE_AUGMENTED: depth (mm) multiplier, > 0;
+                          default 255/4095 (the 12-bit range onto the byte range) */
+    unsigned int flags; /* GMM_FLAG_* for both streams; default 0 */
 } gmm_config;
+
+/* Model structure (§III.B). GMM_MODE_FUSION: a colour mixture (D = 3) and a
+ * depth mixture (D = 1) per pixel, fused by List 1 (§III.C). Depth 0 is "no
+ * reading": the depth mixture is left untouched and its answer is the colour
+ * answer; the depth mixture starts at the first non-zero reading.
+ * GMM_MODE_AUGMENTED: the alternative §III.B sets aside, one mixture per
+ * pixel over (R, G, B, depth_scale * depth) with the colour parameters
+ * (init_var, v_min_c); a zero reading takes the best-ranked component's depth
+ * mean (0 on the first frame). Its foreground is the mask; fg_rgb and fg_d
+ * outputs, if given, receive the same bits. State: w, mu_R, mu_G, mu_B and
+ * v in the colour planes, the depth-channel mean in GMM_PLANE_MU_D; planes
+ * W_D and V_D are zero. */
+#define GMM_MODE_FUSION 0
+#define GMM_MODE_AUGMENTED 1
+
+/* Readings of §III.A the paper leaves open (defaults: neither). The match
+ * test d^2 < k^2 v and the rank key w / sqrt(v) are the same under all.
+ * GMM_FLAG_RHO_ETA: the matched component's mean and variance move with
+ * rho = alpha * N(x; mu, sigma^2 I) (Stauffer-Grimson's second learning
+ * rate), evaluated with the parameters before the update and capped at 1;
+ * default rho = alpha.
+ * GMM_FLAG_VAR_PER_CHANNEL: v tracks the squared distance divided by D (the
+ * per-channel variance sigma^2, so the match test is the Mahalanobis test);
+ * default: v tracks the summed squared distance and sigma^2 = v / D. */
+#define GMM_FLAG_RHO_ETA 1u
+#define GMM_FLAG_VAR_PER_CHANNEL 2u
 
 /* Fill *cfg with the given model parameters and the defaults above. */
 void gmm_config_init(gmm_config *cfg, int H, int W, int M, float alpha,

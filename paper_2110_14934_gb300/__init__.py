@@ -18,7 +18,8 @@ from . import _build
 
 __all__ = ["GMM", "Pool", "GMMError", "fuse_masks", "morph_open3", "mask_words_per_row",
            "state_bytes", "unpack_mask", "pack_mask", "load_library", "PLANES",
-           "PREC_F32", "PREC_F16"]
+           "PREC_F32", "PREC_F16", "make_config", "MODE_FUSION", "MODE_AUGMENTED",
+           "FLAG_RHO_ETA", "FLAG_VAR_PER_CHANNEL"]
 
 OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT = 0, -1, -2, -3, -4, -5
 PLANE_W_C, PLANE_MU_R, PLANE_MU_G, PLANE_MU_B, PLANE_V_C, PLANE_W_D, PLANE_MU_D, PLANE_V_D, \
@@ -27,6 +28,8 @@ PLANES = ("w_c", "mu_r", "mu_g", "mu_b", "v_c", "w_d", "mu_d", "v_d")
 PREC_F32, PREC_F16 = 0, 1
 PIPE_DEPTH = 3
 KERNEL_STAGED, KERNEL_DIRECT = 0, 1
+MODE_FUSION, MODE_AUGMENTED = 0, 1
+FLAG_RHO_ETA, FLAG_VAR_PER_CHANNEL = 1, 2
 
 _ERRNAMES = {EINVAL: "GMM_EINVAL", ENOMEM: "GMM_ENOMEM", ECUDA: "GMM_ECUDA",
              EBUDGET: "GMM_EBUDGET", ETIMEOUT: "GMM_ETIMEOUT"}
@@ -44,7 +47,8 @@ class GMMConfig(ctypes.Structure):
                 ("init_var", ctypes.c_float), ("init_w", ctypes.c_float),
                 ("init_var_d", ctypes.c_float), ("v_min_c", ctypes.c_float),
                 ("v_min_d", ctypes.c_float), ("precision", ctypes.c_int),
-                ("morph_open", ctypes.c_int)]
+                ("morph_open", ctypes.c_int), ("mode", ctypes.c_int),
+                ("depth_scale", ctypes.c_float), ("flags", ctypes.c_uint)]
 
 
 class ServerStats(ctypes.Structure):
@@ -191,23 +195,39 @@ def _check_frame(rgb, depth, H, W):
         raise ValueError(f"depth must be a 16-bit [{H}, {W}] tensor")
 
 
+def make_config(H, W, M=3, alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0, init_w=0.05,
+                init_var_d=None, v_min_c=1.0, v_min_d=1.0, precision=PREC_F32, morph_open=False,
+                mode=MODE_FUSION, depth_scale=None, flags=0) -> GMMConfig:
+    """gmm_config from gmm_config_init's defaults and the given overrides
+    (None keeps the default: init_var_d = init_var, depth_scale = 255/4095)."""
+    cfg = GMMConfig()
+    load_library().gmm_config_init(ctypes.byref(cfg), H, W, M, alpha, match_k, bg_T, init_var,
+                                   init_w)
+    if init_var_d is not None:
+        cfg.init_var_d = init_var_d
+    cfg.v_min_c = v_min_c
+    cfg.v_min_d = v_min_d
+    cfg.precision = precision
+    cfg.morph_open = int(bool(morph_open))
+    cfg.mode = mode
+    if depth_scale is not None:
+        cfg.depth_scale = depth_scale
+    cfg.flags = flags
+    return cfg
+
+
 class GMM:
     """One camera's resident model (FP32 or FP16/BF16 state) on a CUDA device."""
 
     def __init__(self, H, W, M=3, alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0,
                  init_w=0.05, init_var_d=None, v_min_c=1.0, v_min_d=1.0,
-                 precision=PREC_F32, morph_open=False, device=None):
+                 precision=PREC_F32, morph_open=False, mode=MODE_FUSION, depth_scale=None,
+                 flags=0, device=None):
         import torch
         L = load_library()
         self.device = torch.device("cuda" if device is None else device)
-        cfg = GMMConfig()
-        L.gmm_config_init(ctypes.byref(cfg), H, W, M, alpha, match_k, bg_T, init_var, init_w)
-        if init_var_d is not None:
-            cfg.init_var_d = init_var_d
-        cfg.v_min_c = v_min_c
-        cfg.v_min_d = v_min_d
-        cfg.precision = precision
-        cfg.morph_open = int(bool(morph_open))
+        cfg = make_config(H, W, M, alpha, match_k, bg_T, init_var, init_w, init_var_d, v_min_c,
+                          v_min_d, precision, morph_open, mode, depth_scale, flags)
         self.cfg = cfg
         self.H, self.W, self.M = int(H), int(W), int(M)
         self.wpr = mask_words_per_row(W)
@@ -313,17 +333,13 @@ class Pool:
         self.cams = {}
 
     def admit(self, H, W, M=3, alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0, init_w=0.05,
-              init_var_d=None, v_min_c=1.0, v_min_d=1.0) -> int:
+              init_var_d=None, v_min_c=1.0, v_min_d=1.0, mode=MODE_FUSION, depth_scale=None,
+              flags=0) -> int:
         """Returns the camera id; raises GMMError (code EBUDGET) when the state
         budget is exhausted."""
         L = load_library()
-        cfg = GMMConfig()
-        L.gmm_config_init(ctypes.byref(cfg), H, W, M, alpha, match_k, bg_T, init_var, init_w)
-        if init_var_d is not None:
-            cfg.init_var_d = init_var_d
-        cfg.v_min_c = v_min_c
-        cfg.v_min_d = v_min_d
-        cfg.precision = self.precision
+        cfg = make_config(H, W, M, alpha, match_k, bg_T, init_var, init_w, init_var_d, v_min_c,
+                          v_min_d, self.precision, False, mode, depth_scale, flags)
         cam = _check(L.gmm_pool_admit(self._p, ctypes.byref(cfg)))
         self.cams[cam] = (int(H), int(W), int(M))
         return cam
@@ -421,16 +437,12 @@ class Server:
         return float(load_library().gmm_server_now())
 
     def admit(self, H, W, M=3, alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0, init_w=0.05,
-              init_var_d=None, v_min_c=1.0, v_min_d=1.0) -> int:
+              init_var_d=None, v_min_c=1.0, v_min_d=1.0, mode=MODE_FUSION, depth_scale=None,
+              flags=0) -> int:
         """Camera id; raises GMMError with code EBUDGET when rejected."""
         L = load_library()
-        cfg = GMMConfig()
-        L.gmm_config_init(ctypes.byref(cfg), H, W, M, alpha, match_k, bg_T, init_var, init_w)
-        if init_var_d is not None:
-            cfg.init_var_d = init_var_d
-        cfg.v_min_c = v_min_c
-        cfg.v_min_d = v_min_d
-        cfg.precision = self.precision
+        cfg = make_config(H, W, M, alpha, match_k, bg_T, init_var, init_w, init_var_d, v_min_c,
+                          v_min_d, self.precision, False, mode, depth_scale, flags)
         cam = _check(L.gmm_server_admit(self._s, ctypes.byref(cfg)))
         self.cams[cam] = (int(H), int(W), int(M))
         return cam

@@ -88,6 +88,12 @@ std::string check_config(const gmm_config *c) {
         return "precision must be GMM_PREC_F32 or GMM_PREC_F16";
     if (c->morph_open != 0 && c->morph_open != 1)
         return "morph_open must be 0 or 1";
+    if (c->mode != GMM_MODE_FUSION && c->mode != GMM_MODE_AUGMENTED)
+        return "mode must be GMM_MODE_FUSION or GMM_MODE_AUGMENTED";
+    if (!(c->depth_scale > 0.f) || !std::isfinite(c->depth_scale))
+        return "depth_scale must be a finite value > 0";
+    if (c->flags & ~(GMM_FLAG_RHO_ETA | GMM_FLAG_VAR_PER_CHANNEL))
+        return "flags: unknown bits";
     return "";
 }
 
@@ -100,7 +106,7 @@ gmmdev::StreamPrm stream_prm(const gmm_config &c, bool depth) {
     p.init_var = depth ? c.init_var_d : c.init_var;
     p.init_w = c.init_w;
     p.v_min = depth ? c.v_min_d : c.v_min_c;
-    p.pad = 0.f;
+    p.flags = c.flags & (gmmdev::kRhoEta | gmmdev::kVarPerChannel);
     return p;
 }
 
@@ -134,6 +140,9 @@ CamView make_view(const gmm_config &c, const Layout &L, void *arena, const uint8
     }
     v.pc = stream_prm(c, false);
     v.pd = stream_prm(c, true);
+    if (c.mode == GMM_MODE_AUGMENTED)
+        v.flags |= gmmdev::kModeAugmented;
+    v.depth_scale = c.depth_scale;
     return v;
 }
 
@@ -332,7 +341,7 @@ static int launch_apply(gmm_ctx *h, const uint8_t *rgb, const uint16_t *depth, u
     CamView v = make_view(h->cfg, h->L, h->arena, rgb, depth, tick_mask, fgr, fgd,
                           h->initialized ? 0 : 1);
     cudaError_t e;
-    if (h->initialized && h->kernel == GMM_KERNEL_STAGED)
+    if (h->initialized && h->kernel == GMM_KERNEL_STAGED && h->cfg.mode == GMM_MODE_FUSION)
         e = gmmhost::launch_tick_staged(v, h->variant, h->ctas_per_sm, h->d_status, h->stream);
     else
         e = gmmhost::launch_tick(v, 256, h->stream);
@@ -364,6 +373,9 @@ void gmm_config_init(gmm_config *cfg, int H, int W, int M, float alpha, float ma
     cfg->v_min_d = 1.0f;
     cfg->precision = GMM_PREC_F32;
     cfg->morph_open = 0;
+    cfg->mode = GMM_MODE_FUSION;
+    cfg->depth_scale = 255.0f / 4095.0f;
+    cfg->flags = 0u;
 }
 
 int gmm_mask_words_per_row(int W) { return W < 1 ? 0 : (W + 31) / 32; }

@@ -27,11 +27,47 @@ constexpr int kFields = 8;
 constexpr int kTile = 256; // pixels per state tile
 enum { F_WC = 0, F_MUR, F_MUG, F_MUB, F_VC, F_WD, F_MUD, F_VD };
 constexpr uint32_t kDepthStarted = 16u;
-constexpr int kStageInputs = 1;
+constexpr int kStageInputs = 1;   // CamView.flags: frame bytes staged with the state
+constexpr int kModeAugmented = 2; // CamView.flags: one 4-channel mixture (R, G, B, s*depth)
+constexpr uint32_t kRhoEta = 1u;        // StreamPrm.flags: rho = alpha * eta(x | mu, sigma)
+constexpr uint32_t kVarPerChannel = 2u; // StreamPrm.flags: v is the per-channel variance
 
 struct StreamPrm {
-    float alpha, oma, k2, T, init_var, init_w, v_min, pad;
+    float alpha, oma, k2, T, init_var, init_w, v_min;
+    uint32_t flags; // kRhoEta | kVarPerChannel
 };
+
+// Learning rate of the matched component: alpha, or with kRhoEta
+// alpha * N(x; mu, sigma^2 I) (Stauffer-Grimson's rho) from the distance d2
+// and variance v before the update, sigma^2 = v (kVarPerChannel) or v / D,
+// capped at 1. Returns rho and sets orho = 1 - rho (oma exactly by default).
+template <int D>
+__device__ __forceinline__ float match_rate(const StreamPrm &p, float d2, float v, float &orho) {
+    if (!(p.flags & kRhoEta)) {
+        orho = p.oma;
+        return p.alpha;
+    }
+    const float s2 = (p.flags & kVarPerChannel) ? v : v / (float)D;
+    const float base = 6.28318530717958647692f * s2;
+    float norm;
+    if (D == 1)
+        norm = 1.0f / sqrtf(base);
+    else if (D == 3)
+        norm = 1.0f / (base * sqrtf(base));
+    else if (D == 4)
+        norm = 1.0f / (base * base);
+    else
+        norm = powf(base, -0.5f * (float)D);
+    const float rho = fminf(p.alpha * norm * expf(-d2 / (2.0f * s2)), 1.0f);
+    orho = 1.0f - rho;
+    return rho;
+}
+
+// Squared distance that feeds the variance: per channel with kVarPerChannel.
+template <int D>
+__device__ __forceinline__ float var_sample(const StreamPrm &p, float d2) {
+    return (p.flags & kVarPerChannel) ? d2 / (float)D : d2;
+}
 
 // Everything one tick of one camera needs; passed by value to the
 // single-camera kernel, read from a device table by the pooled kernel.
@@ -46,8 +82,9 @@ struct CamView {
     int64_t n_tiles;       // state tiles: ceil(n_pad / kTile)
     int64_t n_pad;         // H*w_pad (< 2^30)
     int H, W, w_pad, wpr;  // wpr = words per mask row = w_pad / 32
-    int M, prec, first, flags; // flags: kStageInputs (set by the staged launcher)
+    int M, prec, first, flags; // flags: kStageInputs (staged launcher), kModeAugmented
     uint32_t wpr_mul, wpr_shift; // n / wpr == umulhi(n, wpr_mul) >> wpr_shift (wpr > 1)
+    float depth_scale, pad2;     // augmented mode: depth (mm) to the colour byte range
     StreamPrm pc, pd;
 };
 
@@ -124,12 +161,16 @@ template <> __device__ __forceinline__ void rank_sort<3, 3>(Comp<3> (&c)[3]) {
 template <> __device__ __forceinline__ void rank_sort<3, 1>(Comp<1> (&c)[3]) {
     comp_swap_if(c[0], c[1]); comp_swap_if(c[0], c[2]); comp_swap_if(c[1], c[2]);
 }
+template <> __device__ __forceinline__ void rank_sort<3, 4>(Comp<4> (&c)[3]) {
+    comp_swap_if(c[0], c[1]); comp_swap_if(c[0], c[2]); comp_swap_if(c[1], c[2]);
+}
 template <int D> __device__ __forceinline__ void net4(Comp<D> (&c)[4]) {
     comp_swap_if(c[0], c[1]); comp_swap_if(c[2], c[3]); comp_swap_if(c[0], c[2]);
     comp_swap_if(c[1], c[3]); comp_swap_if(c[1], c[2]);
 }
 template <> __device__ __forceinline__ void rank_sort<4, 3>(Comp<3> (&c)[4]) { net4(c); }
 template <> __device__ __forceinline__ void rank_sort<4, 1>(Comp<1> (&c)[4]) { net4(c); }
+template <> __device__ __forceinline__ void rank_sort<4, 4>(Comp<4> (&c)[4]) { net4(c); }
 template <int D> __device__ __forceinline__ void net5(Comp<D> (&c)[5]) {
     comp_swap_if(c[0], c[1]); comp_swap_if(c[3], c[4]); comp_swap_if(c[2], c[4]);
     comp_swap_if(c[2], c[3]); comp_swap_if(c[0], c[3]); comp_swap_if(c[0], c[2]);
@@ -137,16 +178,18 @@ template <int D> __device__ __forceinline__ void net5(Comp<D> (&c)[5]) {
 }
 template <> __device__ __forceinline__ void rank_sort<5, 3>(Comp<3> (&c)[5]) { net5(c); }
 template <> __device__ __forceinline__ void rank_sort<5, 1>(Comp<1> (&c)[5]) { net5(c); }
+template <> __device__ __forceinline__ void rank_sort<5, 4>(Comp<4> (&c)[5]) { net5(c); }
 
 // One tick of one mixture at one pixel (§III.A). The components are in rank
 // order on entry and on exit. Returns the stream's foreground bit.
 // kSkipSorted: let a warp skip the sorting network when it would change
 // nothing (pays where issue slots, not HBM, bound the kernel).
-template <int M, int D, bool kSkipSorted>
+template <int M, int D, bool kSkipSorted, bool kOptions>
 __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D],
                                             const StreamPrm &p) {
     // Match: first component, in rank order, within k standard deviations.
     int j = -1;
+    float d2j = 0.f;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         float d2 = 0.f;
@@ -155,8 +198,10 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
             const float df = x[ch] - c[i].mu[ch];
             d2 = fmaf(df, df, d2);
         }
-        if (j < 0 && d2 < p.k2 * c[i].v)
+        if (j < 0 && d2 < p.k2 * c[i].v) {
             j = i;
+            d2j = d2;
+        }
     }
     const bool matched = j >= 0;
     const int jj = matched ? j : M - 1;
@@ -179,15 +224,18 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
         c[i].idx = i;
         if (i == jj) {
             if (matched) {
+                float orho = p.oma, rho = p.alpha;
+                if (kOptions)
+                    rho = match_rate<D>(p, d2j, c[i].v, orho);
                 float d2 = 0.f;
 #pragma unroll
                 for (int ch = 0; ch < D; ++ch) {
-                    const float m = fmaf(p.oma, c[i].mu[ch], p.alpha * x[ch]);
+                    const float m = fmaf(orho, c[i].mu[ch], rho * x[ch]);
                     c[i].mu[ch] = m;
                     const float df = x[ch] - m;
                     d2 = fmaf(df, df, d2);
                 }
-                c[i].v = fmaxf(p.v_min, fmaf(p.oma, c[i].v, p.alpha * d2));
+                c[i].v = fmaxf(p.v_min, fmaf(orho, c[i].v, rho * (kOptions ? var_sample<D>(p, d2) : d2)));
             } else {
 #pragma unroll
                 for (int ch = 0; ch < D; ++ch)
@@ -246,7 +294,10 @@ __device__ __forceinline__ uint32_t fuse_list1(int fgc, int fgd, uint32_t fb) {
 // ------------------------------------------------------------ one pixel
 // p: padded linear pixel index (row * w_pad + x). Returns bit 0 fused label,
 // bit 1 colour foreground, bit 2 depth foreground (all 0 for padding).
-template <int M, int PREC, bool kSkipSorted>
+// kVariant: 0 the paper's method with the default readings; 1 the same with
+// the learning-rate and variance options of StreamPrm.flags honoured; 2 the
+// augmentation alternative (options honoured too).
+template <int M, int PREC, bool kSkipSorted, int kVariant>
 __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) {
     using S = Storage<PREC>;
     const uint32_t p32 = (uint32_t)p;
@@ -262,6 +313,58 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
     // Element of plane 0 for this pixel; plane k lies k * kTile further on.
     const int64_t e0 = (int64_t)(p32 / kTile) * (kFields * M * kTile) + (p32 % kTile);
     const void *pl = cv.planes;
+
+    if (kVariant == 2) {
+        // The augmentation alternative (§III.B): one mixture over R, G, B and
+        // the scaled depth, stored in the colour planes plus the depth-mean
+        // plane. A zero reading takes the best-ranked component's depth mean.
+        Comp<4> a[M];
+        float xa[4] = {xc[0], xc[1], xc[2], cv.depth_scale * (float)draw};
+        int fg;
+        if (cv.first) {
+            if (draw == 0u)
+                xa[3] = 0.f;
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                a[i].w = 1.0f / (float)M;
+                a[i].mu[0] = xa[0]; a[i].mu[1] = xa[1]; a[i].mu[2] = xa[2]; a[i].mu[3] = xa[3];
+                a[i].v = cv.pc.init_var;
+            }
+            fg = 0;
+        } else {
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                const int64_t b = e0 + kFields * i * kTile;
+                a[i].w = S::ldw(pl, b + F_WC * kTile);
+                a[i].mu[0] = S::ldv(pl, b + F_MUR * kTile);
+                a[i].mu[1] = S::ldv(pl, b + F_MUG * kTile);
+                a[i].mu[2] = S::ldv(pl, b + F_MUB * kTile);
+                a[i].mu[3] = S::ldv(pl, b + F_MUD * kTile);
+                a[i].v = S::ldv(pl, b + F_VC * kTile);
+            }
+            if (draw == 0u)
+                xa[3] = a[0].mu[3];
+            fg = mixture_step<M, 4, kSkipSorted, true>(a, xa, cv.pc);
+        }
+        void *plw = cv.planes;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int64_t b = e0 + kFields * i * kTile;
+            S::stw(plw, b + F_WC * kTile, a[i].w);
+            S::stv(plw, b + F_MUR * kTile, a[i].mu[0]);
+            S::stv(plw, b + F_MUG * kTile, a[i].mu[1]);
+            S::stv(plw, b + F_MUB * kTile, a[i].mu[2]);
+            S::stv(plw, b + F_MUD * kTile, a[i].mu[3]);
+            S::stv(plw, b + F_VC * kTile, a[i].v);
+            if (cv.first) { // the unused depth planes read as zero
+                S::stw(plw, b + F_WD * kTile, 0.f);
+                S::stv(plw, b + F_VD * kTile, 0.f);
+            }
+        }
+        const uint32_t f = (uint32_t)fg;
+        cv.fusion[p] = (uint8_t)f;
+        return f | (f << 1) | (f << 2);
+    }
 
     Comp<3> c[M];
     Comp<1> d[M];
@@ -291,7 +394,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
             d[i].mu[0] = S::ldv(pl, b + F_MUD * kTile);
             d[i].v = S::ldv(pl, b + F_VD * kTile);
         }
-        fgc = mixture_step<M, 3, kSkipSorted>(c, xc, cv.pc);
+        fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0)>(c, xc, cv.pc);
     }
 
     if (draw == 0u) {
@@ -306,7 +409,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
         fb |= kDepthStarted;
         fgd = 0;
     } else {
-        fgd = mixture_step<M, 1, kSkipSorted>(d, xd, cv.pd);
+        fgd = mixture_step<M, 1, kSkipSorted, (kVariant != 0)>(d, xd, cv.pd);
     }
     fb = fuse_list1(fgc, fgd, fb);
 

@@ -44,7 +44,15 @@ struct PoolArgs {
     int64_t n_tiles;
 };
 cudaError_t launch_pool_tick_impl(const PoolArgs &a, int threads, int blocks, int prec,
-                                  cudaStream_t s);
+                                  bool all_variants, cudaStream_t s);
+
+// process_pixel variant a camera needs: 0 default, 1 learning-rate/variance
+// options, 2 augmentation alternative.
+__host__ __device__ inline int view_variant(const gmmdev::CamView &cv) {
+    if (cv.flags & gmmdev::kModeAugmented)
+        return 2;
+    return (cv.pc.flags | cv.pd.flags) ? 1 : 0;
+}
 
 int num_sms();
 

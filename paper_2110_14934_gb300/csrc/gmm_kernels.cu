@@ -17,47 +17,72 @@ using gmmhost::PoolArgs;
 namespace {
 
 // ------------------------------------------------------------ single camera
-template <int M, int PREC>
+template <int M, int PREC, int V>
 __device__ __forceinline__ void tick_body(const CamView &cv) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= cv.n_pad) // n_pad is a multiple of 32: whole warps leave
         return;
-    const uint32_t bits = process_pixel<M, PREC, PREC != 0>(cv, p);
+    const uint32_t bits = process_pixel<M, PREC, PREC != 0, V>(cv, p);
     write_mask_words(cv, p >> 5, bits);
 }
 
 // FP32 state: HBM-bound; the register allocation without a residency hint
 // (64 registers, 4 CTAs per SM) measured fastest. FP16/BF16 state: issue
-// bound; at least 4 CTAs per SM.
-template <int M>
-__global__ void __launch_bounds__(256) k_tick_f32(const CamView cv) { tick_body<M, 0>(cv); }
-template <int M>
-__global__ void __launch_bounds__(256, 4) k_tick_f16(const CamView cv) { tick_body<M, 1>(cv); }
+// bound; at least 4 CTAs per SM. V: process_pixel's variant (the options
+// are separate instantiations, so the default kernels carry none of them).
+template <int M, int V>
+__global__ void __launch_bounds__(256) k_tick_f32(const CamView cv) { tick_body<M, 0, V>(cv); }
+template <int M, int V>
+__global__ void __launch_bounds__(256, 4) k_tick_f16(const CamView cv) { tick_body<M, 1, V>(cv); }
+
+template <int M, int PREC, int V>
+cudaError_t launch_tick_v(const CamView &cv, int threads, cudaStream_t s) {
+    const int64_t blocks = (cv.n_pad + threads - 1) / threads;
+    if (PREC == 0)
+        k_tick_f32<M, V><<<(unsigned)blocks, threads, 0, s>>>(cv);
+    else
+        k_tick_f16<M, V><<<(unsigned)blocks, threads, 0, s>>>(cv);
+    return cudaGetLastError();
+}
 
 template <int M, int PREC>
 cudaError_t launch_tick_t(const CamView &cv, int threads, cudaStream_t s) {
-    const int64_t blocks = (cv.n_pad + threads - 1) / threads;
-    if (PREC == 0)
-        k_tick_f32<M><<<(unsigned)blocks, threads, 0, s>>>(cv);
-    else
-        k_tick_f16<M><<<(unsigned)blocks, threads, 0, s>>>(cv);
-    return cudaGetLastError();
+    switch (gmmhost::view_variant(cv)) {
+    case 0: return launch_tick_v<M, PREC, 0>(cv, threads, s);
+    case 1: return launch_tick_v<M, PREC, 1>(cv, threads, s);
+    default: return launch_tick_v<M, PREC, 2>(cv, threads, s);
+    }
 }
 
 // ------------------------------------------------------------ multi camera
 // CTAs take tiles of the implicit worklist (PoolArgs) from an atomic counter;
 // the camera of a tile is found by binary search over tile_begin, and its
 // CamView is staged in shared memory for the whole tile.
-template <int M, int PREC>
+template <int M, int PREC, int V>
 __device__ __forceinline__ void pool_tile(const CamView &cv, int64_t p0, int64_t p1) {
     for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         // p1 - p0 is a multiple of 32 and blockDim too: warps stay whole.
-        const uint32_t bits = process_pixel<M, PREC, true>(cv, p);
+        const uint32_t bits = process_pixel<M, PREC, true, V>(cv, p);
         write_mask_words(cv, p >> 5, bits);
     }
 }
 
-template <int PREC>
+template <int M, int PREC, bool kAll>
+__device__ __forceinline__ void pool_tile_v(const CamView &cv, int64_t p0, int64_t p1) {
+    if (!kAll) {
+        pool_tile<M, PREC, 0>(cv, p0, p1);
+        return;
+    }
+    switch (gmmhost::view_variant(cv)) {
+    case 0: pool_tile<M, PREC, 0>(cv, p0, p1); break;
+    case 1: pool_tile<M, PREC, 1>(cv, p0, p1); break;
+    default: pool_tile<M, PREC, 2>(cv, p0, p1); break;
+    }
+}
+
+// kAll: tiles may come from cameras that use the options or the
+// augmentation alternative (launched only when such a camera is in the tick).
+template <int PREC, bool kAll>
 __global__ void __launch_bounds__(256, PREC == 0 ? 3 : 4) k_pool_tick(const PoolArgs a) {
     __shared__ CamView s_cv;
     __shared__ int64_t s_tile;
@@ -93,9 +118,9 @@ __global__ void __launch_bounds__(256, PREC == 0 ? 3 : 4) k_pool_tick(const Pool
         const int64_t p0 = (t - a.tile_begin[job]) * a.tile_pixels;
         const int64_t p1 = min(p0 + (int64_t)a.tile_pixels, s_cv.n_pad);
         switch (s_cv.M) {
-        case 3: pool_tile<3, PREC>(s_cv, p0, p1); break;
-        case 4: pool_tile<4, PREC>(s_cv, p0, p1); break;
-        default: pool_tile<5, PREC>(s_cv, p0, p1); break;
+        case 3: pool_tile_v<3, PREC, kAll>(s_cv, p0, p1); break;
+        case 4: pool_tile_v<4, PREC, kAll>(s_cv, p0, p1); break;
+        default: pool_tile_v<5, PREC, kAll>(s_cv, p0, p1); break;
         }
         __syncthreads(); // s_cv and s_tile are rewritten next round
     }
@@ -282,11 +307,15 @@ cudaError_t launch_morph_open3(const uint32_t *in, uint32_t *out, int H, int W, 
 }
 
 cudaError_t launch_pool_tick_impl(const PoolArgs &a, int threads, int blocks, int prec,
-                                  cudaStream_t s) {
-    if (prec == 0)
-        k_pool_tick<0><<<blocks, threads, 0, s>>>(a);
+                                  bool all_variants, cudaStream_t s) {
+    if (prec == 0 && !all_variants)
+        k_pool_tick<0, false><<<blocks, threads, 0, s>>>(a);
+    else if (prec == 0)
+        k_pool_tick<0, true><<<blocks, threads, 0, s>>>(a);
+    else if (!all_variants)
+        k_pool_tick<1, false><<<blocks, threads, 0, s>>>(a);
     else
-        k_pool_tick<1><<<blocks, threads, 0, s>>>(a);
+        k_pool_tick<1, true><<<blocks, threads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -317,8 +346,8 @@ cudaError_t launch_confusion(const uint32_t *pred, const uint32_t *truth, int H,
 int pool_max_ctas_per_sm(int prec, int threads) {
     int n = 0;
     cudaError_t e = prec == 0
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool_tick<0>, threads, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool_tick<1>, threads, 0);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool_tick<0, false>, threads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pool_tick<1, false>, threads, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;

@@ -33,9 +33,11 @@ struct PoolCam {
 struct GraphSig {
     int n_jobs = -1, threads = 0, blocks = 0, tile_pixels = 0;
     int64_t n_tiles = -1;
+    bool all_variants = false;
     bool operator==(const GraphSig &o) const {
         return n_jobs == o.n_jobs && threads == o.threads && blocks == o.blocks &&
-               tile_pixels == o.tile_pixels && n_tiles == o.n_tiles;
+               tile_pixels == o.tile_pixels && n_tiles == o.n_tiles &&
+               all_variants == o.all_variants;
     }
 };
 
@@ -89,7 +91,7 @@ static int blocks_for(const gmm_pool *p) {
 
 // Enqueue the tick's table uploads, counter reset and the persistent launch.
 static cudaError_t enqueue_body(gmm_pool *p, cudaStream_t s, int b, int n_jobs, int64_t n_tiles,
-                                int blocks) {
+                                int blocks, bool all_variants) {
     cudaError_t e = cudaMemcpyAsync(p->d_views, p->h_views[b], sizeof(CamView) * n_jobs,
                                     cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
@@ -106,7 +108,7 @@ static cudaError_t enqueue_body(gmm_pool *p, cudaStream_t s, int b, int n_jobs, 
     a.n_jobs = n_jobs;
     a.tile_pixels = p->tile_pixels;
     a.n_tiles = n_tiles;
-    return gmmhost::launch_pool_tick_impl(a, p->threads, blocks, p->prec, s);
+    return gmmhost::launch_pool_tick_impl(a, p->threads, blocks, p->prec, all_variants, s);
 }
 
 // One tick over the submitted cameras. clear: drop the submissions and mark
@@ -126,11 +128,13 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
     }
     int j = 0;
     int64_t tiles = 0;
+    bool all_variants = false; // some camera needs the options or the augmented mixture
     for (PoolCam &c : p->cams) {
         if (!(c.used && c.submitted))
             continue;
         p->h_views[b][j] = make_view(c.cfg, c.L, c.arena, c.rgb, c.depth, c.mask, c.fgr, c.fgd,
                                      c.initialized ? 0 : 1);
+        all_variants = all_variants || gmmhost::view_variant(p->h_views[b][j]) != 0;
         p->h_tile_begin[b][j] = tiles;
         tiles += (c.L.n_pad + p->tile_pixels - 1) / p->tile_pixels;
         ++j;
@@ -145,6 +149,7 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         sig.blocks = blocks;
         sig.tile_pixels = p->tile_pixels;
         sig.n_tiles = tiles;
+        sig.all_variants = all_variants;
         if (!(p->gexec[b] && p->gsig[b] == sig)) {
             if (p->gexec[b])
                 cudaGraphExecDestroy(p->gexec[b]);
@@ -152,7 +157,8 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
             cudaGraph_t g = nullptr;
             e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                const cudaError_t eb = enqueue_body(p, p->cap_stream, b, n_jobs, tiles, blocks);
+                const cudaError_t eb = enqueue_body(p, p->cap_stream, b, n_jobs, tiles, blocks,
+                                                     all_variants);
                 e = cudaStreamEndCapture(p->cap_stream, &g);
                 if (eb != cudaSuccess)
                     e = eb;
@@ -167,7 +173,7 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         if (e == cudaSuccess)
             e = cudaGraphLaunch(p->gexec[b], p->stream);
     } else {
-        e = enqueue_body(p, p->stream, b, n_jobs, tiles, blocks);
+        e = enqueue_body(p, p->stream, b, n_jobs, tiles, blocks, all_variants);
     }
     if (e == cudaSuccess)
         e = cudaEventRecord(p->ev_staged[b], p->stream);

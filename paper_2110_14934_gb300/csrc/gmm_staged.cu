@@ -77,6 +77,7 @@ __device__ __forceinline__ int staged_mixture_step(uint8_t *st, int f0, int t,
     }
     // Match: first component in rank order within k standard deviations.
     int j = -1;
+    float d2j = 0.f;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         float d2 = 0.f;
@@ -85,8 +86,10 @@ __device__ __forceinline__ int staged_mixture_step(uint8_t *st, int f0, int t,
             const float df = x[c] - mu[i][c];
             d2 = fmaf(df, df, d2);
         }
-        if (j < 0 && d2 < p.k2 * v[i])
+        if (j < 0 && d2 < p.k2 * v[i]) {
             j = i;
+            d2j = d2;
+        }
     }
     const bool matched = j >= 0;
     const int jj = matched ? j : M - 1;
@@ -119,14 +122,16 @@ __device__ __forceinline__ int staged_mixture_step(uint8_t *st, int f0, int t,
         w[i] *= inv;
     // The matched component moves toward the sample; a miss starts a new one.
     if (matched) {
+        float orho;
+        const float rho = match_rate<D>(p, d2j, vj, orho);
         float d2 = 0.f;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            muj[c] = fmaf(p.oma, muj[c], p.alpha * x[c]);
+            muj[c] = fmaf(orho, muj[c], rho * x[c]);
             const float df = x[c] - muj[c];
             d2 = fmaf(df, df, d2);
         }
-        vj = fmaxf(p.v_min, fmaf(p.oma, vj, p.alpha * d2));
+        vj = fmaxf(p.v_min, fmaf(orho, vj, rho * var_sample<D>(p, d2)));
     } else {
 #pragma unroll
         for (int c = 0; c < D; ++c)

@@ -36,16 +36,16 @@ class Pair:
     """A GPU model and an oracle model with the same parameters."""
 
     def __init__(self, H, W, M, precision=G.PREC_F32, eps=1e-5, kernel=G.KERNEL_DIRECT,
-                 variant=0, **kw):
+                 variant=0, flags=0, **kw):
         p = dict(DEFAULTS)
         p.update(kw)
         self.H, self.W, self.M = H, W, M
-        self.gpu = G.GMM(H, W, M, precision=precision, **p)
+        self.gpu = G.GMM(H, W, M, precision=precision, flags=flags, **p)
         self.gpu.set_kernel(kernel, variant)
         self.orc = O.OracleGMM(H, W, M, p["alpha"], p["match_k"], p["bg_T"], p["init_var"],
                                p["init_w"], init_var_d=p.get("init_var_d"),
                                v_min_c=p.get("v_min_c", 1.0), v_min_d=p.get("v_min_d", 1.0),
-                               eps=eps)
+                               eps=eps, flags=flags)
 
     def tick(self, rgb, depth):
         """One tick on both; returns (gpu dict of bool masks, oracle dict)."""
@@ -133,3 +133,58 @@ FREE_RUN_EPS = 2e-3
 def scene_frames(seed, H, W, kind, f0, nf):
     s = synth.scene(seed, H, W, kind)
     return synth.frames_host(s, f0, nf)
+
+
+AUG_PLANES = (0, 1, 2, 3, 4, 6)  # planes the augmented mixture keeps
+
+
+class AugPair:
+    """A GPU model in the augmentation mode and the oracle's augmented model."""
+
+    def __init__(self, H, W, M, precision=G.PREC_F32, eps=1e-5, kernel=G.KERNEL_DIRECT,
+                 flags=0, depth_scale=None, **kw):
+        p = dict(DEFAULTS)
+        p.update(kw)
+        self.H, self.W, self.M = H, W, M
+        self.gpu = G.GMM(H, W, M, precision=precision, mode=G.MODE_AUGMENTED, flags=flags,
+                         depth_scale=depth_scale, **p)
+        self.gpu.set_kernel(kernel, 0)
+        ds = O.DEPTH_SCALE_DEFAULT if depth_scale is None else depth_scale
+        self.orc = O.OracleAugmented(H, W, M, p["alpha"], p["match_k"], p["bg_T"],
+                                     p["init_var"], p["init_w"], v_min=p.get("v_min_c", 1.0),
+                                     eps=eps, flags=flags, depth_scale=ds)
+
+    def tick(self, rgb, depth):
+        import torch
+        r, d = to_dev(rgb, depth)
+        wpr = G.mask_words_per_row(self.W)
+        m = torch.empty((self.H, wpr), dtype=torch.int32, device="cuda")
+        fc = torch.empty_like(m)
+        fd = torch.empty_like(m)
+        self.gpu.apply(r, d, m, fc, fd)
+        torch.cuda.synchronize()
+        g = {k: G.unpack_mask(words(t), self.H, self.W)
+             for k, t in (("fused", m), ("fg_rgb", fc), ("fg_d", fd))}
+        return g, self.orc.tick(rgb, depth)
+
+    def sync_oracle_to_gpu(self):
+        self.orc.set_state(self.gpu.planes().astype(np.float64))
+
+    def load_gpu_from_oracle(self):
+        self.gpu.load_state(self.orc.planes().astype(np.float32),
+                            np.zeros((self.H, self.W), np.uint8))
+        self.sync_oracle_to_gpu()
+
+
+def aug_state_mismatch(gpu_planes, orc_planes, exclude=None, rtol=RTOL):
+    """Counts of out-of-tolerance values per kept plane of the augmented
+    state (floors: 1e-3 for the weight, 1 for means and the variance)."""
+    bad, worst = {}, {}
+    for f in AUG_PLANES:
+        o = orc_planes[:, f]
+        err = np.abs(gpu_planes[:, f].astype(np.float64) - o) / np.maximum(np.abs(o), FLOORS[f])
+        if exclude is not None:
+            err = np.where(exclude[None], 0.0, err)
+        bad[f] = int(np.count_nonzero(err > rtol))
+        worst[f] = float(err.max()) if err.size else 0.0
+    return {"bad": bad, "worst": worst}

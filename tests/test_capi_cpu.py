@@ -40,6 +40,18 @@ def test_config_defaults():
     assert (cfg.H, cfg.W, cfg.M) == (480, 640, 3)
     assert cfg.init_var_d == np.float32(225.0) and cfg.v_min_c == 1.0 and cfg.v_min_d == 1.0
     assert cfg.precision == G.PREC_F32 and cfg.morph_open == 0
+    assert cfg.mode == G.MODE_FUSION and cfg.flags == 0
+    assert cfg.depth_scale == np.float32(255.0 / 4095.0)
+
+
+def test_config_struct_matches_header():
+    """The ctypes mirror of gmm_config lists the header's fields in order."""
+    text = open(os.path.join(ROOT, "include", "gmm.h")).read()
+    body = text[text.index("typedef struct gmm_config {"):text.index("} gmm_config;")]
+    names = []
+    for decl in re.findall(r"^\s*(?:unsigned\s+)?(?:int|float)\s+([^;]+);", body, re.M):
+        names += [n.strip() for n in decl.split(",")]
+    assert names == [f[0] for f in G.GMMConfig._fields_]
 
 
 @pytest.mark.parametrize("args,frag", [
@@ -72,7 +84,10 @@ def test_create_ex_rejects_bad_extensions():
     L.gmm_config_init(ctypes.byref(cfg), 48, 64, 4, 0.01, 2.5, 0.7, 225.0, 0.05)
     for field, val, frag in (("v_min_c", 0.0, "floors"), ("v_min_d", -1.0, "floors"),
                              ("init_var_d", 0.0, "init_var_d"), ("precision", 7, "precision"),
-                             ("morph_open", 2, "morph_open")):
+                             ("morph_open", 2, "morph_open"), ("mode", 2, "mode"),
+                             ("depth_scale", 0.0, "depth_scale"),
+                             ("depth_scale", float("inf"), "depth_scale"),
+                             ("flags", 4, "flags")):
         c = G.GMMConfig.from_buffer_copy(cfg)
         setattr(c, field, val)
         assert not L.gmm_create_ex(ctypes.byref(c))

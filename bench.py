@@ -237,6 +237,84 @@ def oracle_rate(wl: dict, frames: int, rows: int, seed: int):
                               f"({rows}x{W} px per frame), FP64, 1 thread"
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_band_worker(bands, warmup, steps, barrier, out):
+    """One oracle process: bands = [(H, W, M, seed, kind, y0, rows, nf)]. Ticks
+    each band `warmup` times (the first tick initialises), waits for the other
+    processes, then times `steps` ticks of every band. Puts (pixels, seconds)."""
+    import oracle as O
+    import synth
+    work = []
+    for (H, W, M, seed, kind, y0, rows, nf) in bands:
+        rgb, dep, _ = synth.rows_host(synth.scene(seed, H, W, kind), 0, nf, y0, rows)
+        g = O.OracleGMM(rows, W, M, **PARAMS)
+        work.append((g, rgb, dep, nf, rows * W))
+    for k in range(warmup):
+        for g, rgb, dep, nf, _ in work:
+            g.tick(rgb[k % nf], dep[k % nf])
+    barrier.wait()
+    t = time.perf_counter()
+    for k in range(steps):
+        for g, rgb, dep, nf, _ in work:
+            f = (warmup + k) % nf
+            g.tick(rgb[f], dep[f])
+    dt = time.perf_counter() - t
+    out.put((steps * sum(w[4] for w in work), dt))
+
+
+def oracle_parallel(bands, warmup, steps, procs):
+    """The oracle, unchanged, in `procs` spawned processes at once, each over
+    its own row bands (pixels are independent, so the split is exact).
+    Returns (Mpixel-frames/s over the slowest process's time, seconds)."""
+    import multiprocessing as mp
+    import oracle as O
+    import synth
+    O.lib()              # built here, before the processes load them
+    synth.host_lib()
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    out = ctx.Queue()
+    per = [[] for _ in range(procs)]
+    for i, b in enumerate(bands):
+        per[i % procs].append(b)
+    ps = [ctx.Process(target=_oracle_band_worker, args=(per[i], warmup, steps, barrier, out))
+          for i in range(procs)]
+    for p_ in ps:
+        p_.start()
+    res = [out.get(timeout=600) for _ in ps]
+    for p_ in ps:
+        p_.join(timeout=60)
+    px = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return px / dt / 1e6, dt
+
+
+def split_rows(H, W, M, seed, kind, y0, rows, nf, parts):
+    """Row band [y0, y0 + rows) cut into at most `parts` contiguous bands."""
+    parts = max(1, min(parts, rows))
+    cuts = [y0 + (rows * i) // parts for i in range(parts + 1)]
+    return [(H, W, M, seed, kind, cuts[i], cuts[i + 1] - cuts[i], nf)
+            for i in range(parts) if cuts[i + 1] > cuts[i]]
+
+
+def oracle_all_cores(wl, frames, seed):
+    """The oracle over every row of `frames` frames of the workload's camera,
+    one band of rows per host core. Returns (Mpixel-frames/s, seconds, cores,
+    sample description)."""
+    H, W, M = wl["H"], wl["W"], wl["M"]
+    n = host_cores()
+    bands = split_rows(H, W, M, seed, wl["kind"], 0, H, frames, n)
+    v, dt = oracle_parallel(bands, 1, frames - 1, len(bands))
+    return v, dt, len(bands), (f"frames 1-{frames - 1} of the sequence, all {H}x{W} px, "
+                               f"{len(bands)} processes over row bands, FP64")
+
+
 def reference_cameras(wl):
     """(H, W, M, seed, scene kind) the reference arm samples: the workload's
     camera, or one camera per resolution of a many-camera mix."""
@@ -250,34 +328,26 @@ def run_reference(args, wl):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    import oracle as O
-    import synth
     cams = reference_cameras(wl)
     steps = args.steps + args.warmup
-    # size each step's sample so that warmup + steps take about a minute
+    procs = host_cores()
+    # size each step's sample so that warmup + steps take about a minute on
+    # all host cores (one process per core, each over its own rows)
     H0, W0, M0, s0, k0 = max(cams, key=lambda c: c[0] * c[1])
     probe_rate, _, _ = oracle_rate(dict(H=H0, W=W0, M=M0, kind=k0), 3, 16, s0)
     target_s = float(os.environ.get("GMM_REFERENCE_SECONDS", "60"))
-    px_per_cam = target_s * probe_rate * 1e6 / max(steps, 1) / len(cams)
+    px_per_cam = target_s * probe_rate * procs * 1e6 / max(steps, 1) / len(cams)
     bands, descr = [], []
     for (H, W, M, seed, kind) in cams:
         rows = int(max(1, min(H, px_per_cam / W)))
         y0 = (H - rows) // 2
         nf = min(wl["frames"], steps + 1)
-        rgb, dep, _ = synth.rows_host(synth.scene(seed, H, W, kind), 0, nf, y0, rows)
-        bands.append((O.OracleGMM(rows, W, M, **PARAMS), rgb, dep, nf, rows * W))
+        bands += split_rows(H, W, M, seed, kind, y0, rows, nf, procs)
         descr.append(f"rows {y0}-{y0 + rows - 1} of a {W}x{H} M={M} camera")
-    for k in range(args.warmup):
-        for g, rgb, dep, nf, _ in bands:
-            g.tick(rgb[k % nf], dep[k % nf])
-    t = time.perf_counter()
-    for k in range(args.steps):
-        for g, rgb, dep, nf, _ in bands:
-            f = (args.warmup + k) % nf
-            g.tick(rgb[f], dep[f])
-    dt = time.perf_counter() - t
-    value = args.steps * sum(b[4] for b in bands) / dt / 1e6
-    sample = "each step: " + "; ".join(descr) + " (one frame each), FP64, 1 thread"
+    procs = min(procs, len(bands))
+    value, dt = oracle_parallel(bands, args.warmup, args.steps, procs)
+    sample = ("each step: " + "; ".join(descr) + f" (one frame each), FP64, {procs} processes "
+              "over row bands")
     cfg = (pool_config(args.workload, wl, world, camera_mix(wl["cams_per_res"], 0), None, None)
            if (wl.get("pool") or wl.get("serve")) else config_dict(args.workload, wl, world))
     line = {
@@ -285,7 +355,8 @@ def run_reference(args, wl):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": cfg,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -325,15 +396,28 @@ def run_gmm(args, wl):
     g.set_kernel(KERNELS[args.kernel], args.variant, args.ctas)
     mask = g.new_mask()
     K, Wm = args.steps, args.warmup
+    # --morph: each step also runs the 3x3 opening of the fused mask (the
+    # tick writes a scratch mask, gmm_morph_open3 the output), with an event
+    # between the two launches to time each kernel.
+    tick_mask = g.new_mask() if args.morph else mask
+
+    def step(f, mid=None):
+        g.apply(rgb_d[f], dep_d[f], tick_mask, stream=stream)
+        if args.morph:
+            if mid is not None:
+                mid.record(stream)
+            G.morph_open3(tick_mask, mask, H, W, stream=stream)
 
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
         clocks.wait_first()
     for k in range(Wm):
-        g.apply(rgb_d[k % nf], dep_d[k % nf], mask, stream=stream)
+        step(k % nf)
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    marks = ([(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)] if args.morph else None)
     barrier(world, dev)
     torch.cuda.synchronize()
     if clocks:
@@ -341,7 +425,11 @@ def run_gmm(args, wl):
     t_start.record(stream)
     for k in range(K):
         f = (Wm + k) % nf
-        g.apply(rgb_d[f], dep_d[f], mask, stream=stream)
+        if marks:
+            marks[k][0].record(stream)
+            step(f, marks[k][1])
+        else:
+            step(f)
     t_end.record(stream)
     torch.cuda.synchronize()
     barrier(world, dev)
@@ -351,11 +439,25 @@ def run_gmm(args, wl):
     total_ms = reduce_max(local_ms, world, dev)
     value = aggregate_mpx_per_s(world, K, H * W, total_ms)
 
-    # Roofline of the tick kernel: it is the only work in the timed region
-    # (one launch per step, back to back on one stream), so its average
-    # launch duration is the region's event time over K.
+    # Roofline of the tick kernel. Without --morph it is the only work in the
+    # timed region (one launch per step, back to back on one stream), so its
+    # average launch duration is the region's event time over K; with --morph
+    # the events around each launch give both kernels' durations.
     bpp = bytes_per_pixel(M, prec)
-    avg_kernel_s = local_ms / K / 1e3
+    morph_info = None
+    if marks:
+        tick_ms_sum = sum(a.elapsed_time(b) for a, b in marks)
+        ends_next = [marks[k + 1][0] for k in range(K - 1)] + [t_end]
+        morph_ms_sum = sum(marks[k][1].elapsed_time(ends_next[k]) for k in range(K))
+        avg_kernel_s = tick_ms_sum / K / 1e3
+        morph_s = morph_ms_sum / K / 1e3
+        morph_bytes = 2 * H * G.mask_words_per_row(W) * 4
+        morph_info = {"kernel": "k_morph_open3", "avg_us": morph_s * 1e6,
+                      "algorithmic_bytes_per_launch": morph_bytes,
+                      "achieved_gbs": morph_bytes / morph_s / 1e9,
+                      "share_of_step": morph_ms_sum / local_ms}
+    else:
+        avg_kernel_s = local_ms / K / 1e3
     achieved = H * W * bpp / avg_kernel_s / 1e9
 
     # Per-tick device latency: a separate pass with an event pair per tick.
@@ -365,7 +467,7 @@ def run_gmm(args, wl):
     for k in range(n_lat):
         f = (Wm + K + k) % nf
         starts[k].record(stream)
-        g.apply(rgb_d[f], dep_d[f], mask, stream=stream)
+        step(f)
         ends[k].record(stream)
     torch.cuda.synchronize()
     tick_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -375,13 +477,19 @@ def run_gmm(args, wl):
     # end to end through the host-memory C-ABI path (pipelined, Fig. 4(a))
     e2e = run_e2e(G, torch, g_args=(H, W, M, prec), frames=(rgb_d, dep_d), dev=dev,
                   steps=args.e2e_steps or K, warmup=Wm, world=world,
-                  kernel=(KERNELS[args.kernel], args.variant, args.ctas))
+                  kernel=(KERNELS[args.kernel], args.variant, args.ctas), morph=args.morph)
     del rgb_d, dep_d
     cpu = None
     if rank == 0 and world == 1 and args.cpu_frames > 0:
-        v, secs, sample = oracle_rate(wl, args.cpu_frames, args.cpu_rows or H, rank_seed(1, 0))
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-               "seconds": secs}
+        v1, secs1, sample1 = oracle_rate(wl, args.cpu_frames, args.cpu_rows or H, rank_seed(1, 0))
+        if args.cpu_all_frames > 1:
+            v, secs, cores, sample = oracle_all_cores(wl, args.cpu_all_frames, rank_seed(1, 0))
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                   "seconds": secs, "single_thread": {"value": v1, "cores": 1,
+                                                      "sample": sample1, "seconds": secs1}}
+        else:
+            cpu = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample1,
+                   "seconds": secs1}
     if clocks:
         clk = clocks.summary()
         clocks.close()
@@ -404,9 +512,12 @@ def run_gmm(args, wl):
                     "d2h_bytes_per_step": e2e["d2h"], "path": "gmm_pipe_submit/gmm_pipe_wait, "
                     "pinned host frames, 3 frames in flight"},
             "cpu_baseline": cpu,
-            "gpu_launches": K,
+            "gpu_launches": K * (2 if args.morph else 1),
             "clocks": clk if clocks else None,
         }
+        if morph_info:
+            line["config"]["morph_open"] = True
+            line["morph"] = morph_info
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -853,7 +964,7 @@ def pct(sorted_vals, p):
     return sorted_vals[i]
 
 
-def run_e2e(G, torch, g_args, frames, dev, steps, warmup, world, kernel):
+def run_e2e(G, torch, g_args, frames, dev, steps, warmup, world, kernel, morph=False):
     """Host frames (pinned) -> C-ABI pipelined path -> host masks. Timed from
     the first submit to the last mask in host memory; per-frame latency from a
     separate unpipelined pass (submit, wait)."""
@@ -866,7 +977,7 @@ def run_e2e(G, torch, g_args, frames, dev, steps, warmup, world, kernel):
     dep_h.copy_(dep_d[:n_host])
     ring = 8
     masks = torch.empty((ring, H, G.mask_words_per_row(W)), dtype=torch.int32).pin_memory()
-    g = G.GMM(H, W, M, precision=prec, device=dev, **PARAMS)
+    g = G.GMM(H, W, M, precision=prec, device=dev, morph_open=morph, **PARAMS)
     g.set_kernel(*kernel)
     g.set_stream(torch.cuda.current_stream(dev))
     pending = []
@@ -922,8 +1033,12 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="pooled workloads: default launch")
     ap.add_argument("--frames", type=int, default=0,
                     help="resident frames to cycle through (0: the workload's sequence length)")
+    ap.add_argument("--morph", action="store_true",
+                    help="single-camera workloads: each step adds the 3x3 opening of the mask")
     ap.add_argument("--cpu-frames", type=int, default=21, help="oracle baseline frames (0 = skip)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle baseline rows per frame (0 = all)")
+    ap.add_argument("--cpu-all-frames", type=int, default=61,
+                    help="frames of the all-core oracle baseline (0 = single thread only)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -1,7 +1,8 @@
 """Recall, precision and F1 (Eq. 1-3, §V.A) counted on the GPU, and the
 accuracy claims they support: after a global illumination change the colour
 foreground fails while depth holds, and the fused answer stays close to the
-ground truth (§V.A); FP16/BF16 state gives the same accuracy as FP32."""
+ground truth (§V.A); the augmentation alternative behaves like colour alone
+(§III.B); FP16/BF16 state gives the same accuracy as FP32."""
 import numpy as np
 import pytest
 
@@ -74,3 +75,34 @@ def test_fp16_state_has_the_same_accuracy():
     b = _f1_series(G.PREC_F16, (rgb, depth), gt, H, W, M=5)
     for k in a:
         assert abs(a[k][10:].mean() - b[k][10:].mean()) < 0.01, k
+
+
+def test_augmentation_behaves_like_colour_alone():
+    """§III.B (Fig. 2): one mixture over R, G, B and the scaled depth keeps the
+    colour model's failure under the illumination step, since the depth
+    channel is outweighed by the three colour channels. On the same scene as
+    above the augmented mask's F1 after the step is within 0.05 of the colour
+    mask's and far below the depth mask's and the fused mask's (the oracle
+    gives 0.223 augmented, 0.231 colour, 0.776 depth, 0.418 fused over frames
+    52-79; 0.597, 0.629, 0.748, 0.840 over frames 80-89)."""
+    import torch
+    H, W = 480, 640
+    rgb, depth, gt = synth.frames_host(synth.scene(1, H, W, 0), 0, 90)
+    f1 = _f1_series(G.PREC_F32, (rgb, depth), gt, H, W)
+    g = G.GMM(H, W, 3, mode=G.MODE_AUGMENTED)
+    aug = []
+    for t in range(90):
+        r, d = to_dev(rgb[t], depth[t])
+        m = g.apply(r, d)
+        truth = G.pack_mask_device(torch.from_numpy(gt[t]).cuda(), H, W)
+        aug.append(G.mask_scores(m, truth, H, W)["f1"])
+    aug = np.array(aug)
+    after, late = slice(52, 80), slice(80, 90)
+    assert abs(aug[after].mean() - f1["fg_rgb"][after].mean()) < 0.05
+    assert abs(aug[late].mean() - f1["fg_rgb"][late].mean()) < 0.1
+    assert aug[after].mean() < f1["fg_d"][after].mean() - 0.3
+    assert aug[after].mean() < f1["fused"][after].mean() - 0.1
+    assert aug[late].mean() < f1["fused"][late].mean() - 0.1
+    print("mean F1 after the step: augmented %.3f rgb %.3f depth %.3f fused %.3f" % (
+        aug[after].mean(), f1["fg_rgb"][after].mean(), f1["fg_d"][after].mean(),
+        f1["fused"][after].mean()))

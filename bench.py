@@ -315,6 +315,30 @@ def oracle_all_cores(wl, frames, seed):
                                f"{len(bands)} processes over row bands, FP64")
 
 
+def oracle_many_cameras(wl, seconds: float):
+    """The oracle on all host cores over a band of rows of one camera per
+    resolution of a many-camera workload, each band ticking through
+    consecutive frames; sized for about `seconds` of wall time. Returns the
+    cpu_baseline dict."""
+    cams = reference_cameras(wl)
+    procs = host_cores()
+    H0, W0, M0, s0, k0 = max(cams, key=lambda c: c[0] * c[1])
+    probe_rate, _, _ = oracle_rate(dict(H=H0, W=W0, M=M0, kind=k0), 3, 16, s0)
+    steps = 8
+    px_per_cam = seconds * probe_rate * procs * 1e6 / (steps + 1) / len(cams)
+    bands, descr = [], []
+    for (H, W, M, seed, kind) in cams:
+        rows = int(max(1, min(H, px_per_cam / W)))
+        y0 = (H - rows) // 2
+        bands += split_rows(H, W, M, seed, kind, y0, rows, steps + 1, procs)
+        descr.append(f"rows {y0}-{y0 + rows - 1} of a {W}x{H} M={M} camera")
+    procs = min(procs, len(bands))
+    value, dt = oracle_parallel(bands, 1, steps, procs)
+    return {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"frames 1-{steps}: " + "; ".join(descr) + f", FP64, {procs} processes "
+                      "over row bands", "seconds": dt}
+
+
 def reference_cameras(wl):
     """(H, W, M, seed, scene kind) the reference arm samples: the workload's
     camera, or one camera per resolution of a many-camera mix."""
@@ -661,6 +685,8 @@ def run_pool(args, wl):
 
     e2e = run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, args.e2e_steps or min(K, 600),
                        Wm, world)
+    cpu = (oracle_many_cameras(wl, args.cpu_seconds)
+           if rank == 0 and world == 1 and args.cpu_seconds > 0 else None)
     clk = None
     if clocks:
         clk = clocks.summary()
@@ -683,7 +709,7 @@ def run_pool(args, wl):
                     "d2h_bytes_per_step": e2e["d2h"],
                     "path": "pinned packed tick-sets -> device staging (copy stream) -> "
                             "gmm_pool_submit_many + gmm_pool_tick -> masks to pinned host"},
-            "cpu_baseline": None,
+            "cpu_baseline": cpu,
             "gpu_launches": K,
             "clocks": clk,
         }
@@ -912,6 +938,8 @@ def run_serving(args, wl):
         sum(H * W for (H, W, _, _) in cams)
     achieved = pixels * mean_bpp / wall / 1e9
     peak, peak_src = measured_hbm_peak()
+    cpu = (oracle_many_cameras(wl, args.cpu_seconds)
+           if rank == 0 and world == 1 and args.cpu_seconds > 0 else None)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -942,7 +970,7 @@ def run_serving(args, wl):
                     "h2d_bytes_per_step": int(pixels * 5 / max(st["ticks"], 1)),
                     "d2h_bytes_per_step": int(pixels / 8 / max(st["ticks"], 1)),
                     "path": "page-locked host frames -> gmm_server_push -> masks in host memory"},
-            "cpu_baseline": None,
+            "cpu_baseline": cpu,
             "gpu_launches": st["ticks"],
             "clocks": None,
         }
@@ -1037,6 +1065,9 @@ def main(argv=None):
                     help="single-camera workloads: each step adds the 3x3 opening of the mask")
     ap.add_argument("--cpu-frames", type=int, default=21, help="oracle baseline frames (0 = skip)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle baseline rows per frame (0 = all)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="many-camera workloads: wall seconds of the all-core oracle baseline "
+                         "(0 = skip)")
     ap.add_argument("--cpu-all-frames", type=int, default=61,
                     help="frames of the all-core oracle baseline (0 = single thread only)")
     args = ap.parse_args(argv)

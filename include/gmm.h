@@ -150,6 +150,16 @@ gmm_t *gmm_create_ex(const gmm_config *cfg);
  * default stream). The caller keeps the stream alive. */
 int gmm_set_stream(gmm_t *h, void *cuda_stream);
 
+/* Self-test of the bounded device wait the staged kernel relies on (no
+ * counterpart in the paper). Launches one thread that waits on a barrier
+ * that nothing completes, with the same time-bounded wait; the wait must run
+ * out after timeout_ms (1..2000), the kernel records it and returns, and the
+ * context stays usable. On GMM_OK, *timed_out = 1 if the device reported the
+ * timeout and *waited_ms the time it waited. Synchronous on the current
+ * device; allocates 16 bytes of device memory for the results. GMM_EINVAL
+ * for out-of-range arguments, GMM_ECUDA if a CUDA call fails. */
+int gmm_wait_selftest(int timeout_ms, int *timed_out, double *waited_ms);
+
 /* Tick kernel of the handle (§IV: the per-pixel GPU pass). Both compute the
  * same arithmetic bit for bit. GMM_KERNEL_DIRECT (default): one thread per
  * pixel, coalesced loads and stores straight from and to HBM (always used
@@ -270,11 +280,15 @@ int gmm_mask_confusion(const uint32_t *pred, const uint32_t *truth, int H, int W
  *
  * The caller provides the model state: `state` is device memory of
  * gmm_state_bytes(H, W, M, precision) bytes, 16-byte aligned. Pixels are
- * numbered p = y*Wp + x with Wp = ceil(W/32)*32 and grouped in tiles of 256:
- * tile t holds M*8 planes of 256 elements (plane 8*i + GMM_PLANE_*, i the
- * rank; float32, or bfloat16 weights and float16 means and variances), so
- * element (plane k, pixel p) is at index ((p/256)*8*M + k)*256 + p%256;
- * the ceil(H*Wp/256) tiles are followed by one List-1 byte per tiled pixel. The state
+ * numbered p = y*Wp + x with Wp = ceil(W/32)*32 and grouped in tiles of 256
+ * pixels of 8*M*256 elements each (i the rank, f a GMM_PLANE_* field).
+ * GMM_PREC_F32: float32; field f of component i at pixel p is element
+ * ((p/256)*8*M + 8*i + f)*256 + p%256. GMM_PREC_F16: 2-byte elements
+ * (bfloat16 weights, float16 means and variances); per component and pixel
+ * two groups of four slots, group 0 = {W_C, W_D, MU_R, MU_G}, group 1 =
+ * {MU_B, V_C, MU_D, V_D}; field f of component i at pixel p is element
+ * (p/256)*8*M*256 + ((2*i + group)*256 + p%256)*4 + slot.
+ * The ceil(H*Wp/256) tiles are followed by one List-1 byte per tiled pixel. The state
  * persists between calls; first = 1 initialises it from this frame (it
  * need not be cleared beforehand), first = 0 updates it. cfg gives the
  * model parameters (its morph_open field is ignored). rgb8, depth16 and

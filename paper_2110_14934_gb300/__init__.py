@@ -81,6 +81,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_create_ex": (_vp, [ctypes.POINTER(GMMConfig)]),
         "gmm_set_stream": (ctypes.c_int, [_vp, _vp]),
         "gmm_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "gmm_wait_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_double)]),
         "gmm_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         "gmm_apply_ex": (ctypes.c_int, [_vp] * 6),
         "gmm_apply_host": (ctypes.c_int, [_vp] * 4),
@@ -520,6 +522,14 @@ def mask_scores(pred, truth, H, W, counts=None, stream=None) -> dict:
     P = tp / (tp + fp) if tp + fp else 0.0
     F1 = 2 * P * R / (P + R) if P + R else 0.0
     return {"tp": tp, "fp": fp, "fn": fn, "tn": tn, "recall": R, "precision": P, "f1": F1}
+
+
+def wait_selftest(timeout_ms: int = 200) -> dict:
+    """Run the bounded-wait self-test on the current CUDA device: a device
+    wait that nothing completes must give up after timeout_ms and report it."""
+    t, w = ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(load_library().gmm_wait_selftest(int(timeout_ms), ctypes.byref(t), ctypes.byref(w)))
+    return {"timed_out": bool(t.value), "waited_ms": w.value}
 
 
 def morph_open3(mask_in, mask_out, H, W, stream=None) -> None:

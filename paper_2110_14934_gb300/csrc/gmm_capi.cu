@@ -173,12 +173,13 @@ std::string check_frame_ptrs(const uint8_t *rgb, const uint16_t *depth, uint32_t
 }
 
 // Host-side conversion of one plane between the device layout (padded rows,
-// storage type) and row-major floats.
-void plane_to_float(const void *src, int elem, bool weight, const Layout &L, int H, int W,
-                    float *dst) {
+// storage type) and row-major floats. src/dst hold the plane's value of
+// padded pixel p at element p * stride + slot.
+void plane_to_float(const void *src, int elem, bool weight, int stride, int slot,
+                    const Layout &L, int H, int W, float *dst) {
     for (int y = 0; y < H; ++y) {
         for (int x = 0; x < W; ++x) {
-            const int64_t p = (int64_t)y * L.w_pad + x;
+            const int64_t p = ((int64_t)y * L.w_pad + x) * stride + slot;
             float v;
             if (elem == 4)
                 v = static_cast<const float *>(src)[p];
@@ -191,21 +192,44 @@ void plane_to_float(const void *src, int elem, bool weight, const Layout &L, int
     }
 }
 
-void float_to_plane(const float *src, int elem, bool weight, const Layout &L, int H, int W,
-                    void *dst) {
-    std::memset(dst, 0, (size_t)L.n_pad * elem);
-    for (int y = 0; y < H; ++y) {
-        for (int x = 0; x < W; ++x) {
-            const int64_t p = (int64_t)y * L.w_pad + x;
-            const float v = src[(int64_t)y * W + x];
-            if (elem == 4)
-                static_cast<float *>(dst)[p] = v;
-            else if (weight)
-                static_cast<__nv_bfloat16 *>(dst)[p] = __float2bfloat16_rn(v);
-            else
-                static_cast<__half *>(dst)[p] = __float2half_rn(fminf(v, 65504.0f));
-        }
+// Writes the plane's values into dst (other slots untouched); padded pixels
+// get 0.
+void float_to_plane(const float *src, int elem, bool weight, int stride, int slot,
+                    const Layout &L, int H, int W, void *dst) {
+    for (int64_t q = 0; q < L.n_pad; ++q) {
+        const int64_t y = q / L.w_pad, x = q % L.w_pad;
+        const float v = (y < H && x < W) ? src[y * W + x] : 0.f;
+        const int64_t p = q * stride + slot;
+        if (elem == 4)
+            static_cast<float *>(dst)[p] = v;
+        else if (weight)
+            static_cast<__nv_bfloat16 *>(dst)[p] = __float2bfloat16_rn(v);
+        else
+            static_cast<__half *>(dst)[p] = __float2half_rn(fminf(v, 65504.0f));
     }
+}
+
+// Where one plane lives: in every tile, a run of `run` bytes starting `off`
+// bytes into the tile, holding its value of tile pixel t at element
+// t * stride + slot (FP32: the plane itself; FP16/BF16: its group).
+struct PlaneRun {
+    size_t off, run;
+    int stride, slot;
+};
+PlaneRun plane_run(const Layout &L, int comp, int plane) {
+    PlaneRun r;
+    if (L.elem == 4) {
+        r.run = (size_t)gmmdev::kTile * 4;
+        r.off = (size_t)gmmdev::tile_elem<0>(comp, plane, 0) * 4;
+        r.stride = 1;
+        r.slot = 0;
+    } else {
+        r.run = (size_t)gmmdev::kTile * 8;
+        r.off = (size_t)gmmdev::tile_elem<1>(comp, plane, 0) / 4 * 8;
+        r.stride = 4;
+        r.slot = gmmdev::h16_slot(plane);
+    }
+    return r;
 }
 
 int state_get_common(const gmm_config &c, const Layout &L, const void *arena,
@@ -232,19 +256,18 @@ int state_get_common(const gmm_config &c, const Layout &L, const void *arena,
                 dst[(int64_t)y * c.W + x] = (float)tmp[(size_t)y * L.w_pad + x];
         return GMM_OK;
     }
-    const int pi = comp * gmmdev::kFields + plane;
     const bool weight = plane == GMM_PLANE_W_C || plane == GMM_PLANE_W_D;
-    // One plane is a kTile-element run in every tile: a pitched copy.
-    const size_t run = (size_t)gmmdev::kTile * L.elem;
-    std::vector<uint8_t> tmp((size_t)L.n_tiles * run);
-    const uint8_t *src = static_cast<const uint8_t *>(arena) + (size_t)pi * run;
-    cudaError_t e = cudaMemcpy2DAsync(tmp.data(), run, src, L.tile_bytes, run, (size_t)L.n_tiles,
-                                      cudaMemcpyDeviceToHost, stream);
+    // The plane (or its group) is a run of bytes in every tile: a pitched copy.
+    const PlaneRun r = plane_run(L, comp, plane);
+    std::vector<uint8_t> tmp((size_t)L.n_tiles * r.run);
+    const uint8_t *src = static_cast<const uint8_t *>(arena) + r.off;
+    cudaError_t e = cudaMemcpy2DAsync(tmp.data(), r.run, src, L.tile_bytes, r.run,
+                                      (size_t)L.n_tiles, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess)
         return cuda_fail(sticky, e, "gmm_state_get");
-    plane_to_float(tmp.data(), L.elem, weight, L, c.H, c.W, dst);
+    plane_to_float(tmp.data(), L.elem, weight, r.stride, r.slot, L, c.H, c.W, dst);
     return GMM_OK;
 }
 
@@ -272,14 +295,21 @@ int state_set_common(const gmm_config &c, const Layout &L, void *arena, cudaStre
         if (e == cudaSuccess)
             e = cudaStreamSynchronize(stream);
     } else {
-        const int pi = comp * gmmdev::kFields + plane;
         const bool weight = plane == GMM_PLANE_W_C || plane == GMM_PLANE_W_D;
-        const size_t run = (size_t)gmmdev::kTile * L.elem;
-        std::vector<uint8_t> tmp((size_t)L.n_tiles * run, 0);
-        float_to_plane(src, L.elem, weight, L, c.H, c.W, tmp.data());
-        uint8_t *dst = static_cast<uint8_t *>(arena) + (size_t)pi * run;
-        e = cudaMemcpy2DAsync(dst, L.tile_bytes, tmp.data(), run, run, (size_t)L.n_tiles,
-                              cudaMemcpyHostToDevice, stream);
+        const PlaneRun r = plane_run(L, comp, plane);
+        std::vector<uint8_t> tmp((size_t)L.n_tiles * r.run, 0);
+        uint8_t *dst = static_cast<uint8_t *>(arena) + r.off;
+        e = cudaSuccess;
+        if (r.stride > 1) // the group's other slots keep their values
+            e = cudaMemcpy2DAsync(tmp.data(), r.run, dst, L.tile_bytes, r.run,
+                                  (size_t)L.n_tiles, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(stream);
+        if (e == cudaSuccess) {
+            float_to_plane(src, L.elem, weight, r.stride, r.slot, L, c.H, c.W, tmp.data());
+            e = cudaMemcpy2DAsync(dst, L.tile_bytes, tmp.data(), r.run, r.run,
+                                  (size_t)L.n_tiles, cudaMemcpyHostToDevice, stream);
+        }
         if (e == cudaSuccess)
             e = cudaStreamSynchronize(stream);
     }
@@ -611,6 +641,35 @@ int gmm_sync(gmm_t *h) {
     if (status != 0)
         return fail(GMM_ETIMEOUT, "gmm_sync: a staged-kernel pipeline wait ran out");
     return h->sticky == cudaSuccess ? GMM_OK : fail(GMM_ECUDA, "gmm_sync: earlier CUDA failure");
+}
+
+int gmm_wait_selftest(int timeout_ms, int *timed_out, double *waited_ms) {
+    if (timeout_ms < 1 || timeout_ms > 2000 || !timed_out || !waited_ms)
+        return fail(GMM_EINVAL, "gmm_wait_selftest: timeout_ms in [1, 2000] and outputs required");
+    void *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 16);
+    if (e == cudaSuccess)
+        e = cudaMemset(buf, 0, 16);
+    int *status = static_cast<int *>(buf);
+    unsigned long long *waited = reinterpret_cast<unsigned long long *>(static_cast<char *>(buf) + 8);
+    if (e == cudaSuccess)
+        e = gmmhost::launch_wait_selftest(status, waited, (unsigned long long)timeout_ms * 1000000ull,
+                                          nullptr);
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    int st = 0;
+    unsigned long long ns = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&st, status, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&ns, waited, sizeof(ns), cudaMemcpyDeviceToHost);
+    if (buf)
+        cudaFree(buf);
+    if (e != cudaSuccess)
+        return fail(GMM_ECUDA, std::string("gmm_wait_selftest: ") + cudaGetErrorString(e));
+    *timed_out = st & 1;
+    *waited_ms = (double)ns * 1e-6;
+    return GMM_OK;
 }
 
 int gmm_set_kernel(gmm_t *h, int kind, int variant, int ctas_per_sm) {

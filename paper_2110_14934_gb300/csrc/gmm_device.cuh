@@ -6,15 +6,21 @@
 // State layout in device memory (one camera). Pixels are numbered in padded
 // row-major order p = row * w_pad + x (rows padded to a multiple of 32 pixels,
 // so the 32 pixels of a warp map to one mask word) and grouped into tiles of
-// kTile = 256 consecutive pixels. Each tile stores its M*8 planes
-// contiguously, component-major: plane 8*i + field (fields w_c, mu_r, mu_g,
-// mu_b, v_c, w_d, mu_d, v_d; i the rank), kTile elements each. Element
-// (plane k, pixel p) sits at ((p / kTile) * 8M + k) * kTile + p % kTile.
-// A warp reads 32 consecutive elements of a plane (one fully used 128-byte
-// line in FP32); the plane offsets of a pixel are compile-time constants
-// from one base address; and a tile's whole state is one contiguous block
-// that a single bulk copy moves. The List-1 byte of a pixel lives in a
-// separate byte array indexed by p (n_tiles * kTile bytes).
+// kTile = 256 consecutive pixels. Each tile stores the 8M values of its
+// pixels contiguously (8M * kTile elements), component-major (i the rank;
+// fields w_c, mu_r, mu_g, mu_b, v_c, w_d, mu_d, v_d):
+//   FP32: one plane per field, element (8 i + field) * kTile + t for tile
+//         pixel t: a warp reads 32 consecutive floats of a plane, one fully
+//         used 128-byte line;
+//   FP16/BF16: two groups of four 2-byte slots per component and pixel,
+//         group 0 = {w_c, w_d, mu_r, mu_g}, group 1 = {mu_b, v_c, mu_d, v_d},
+//         element ((2 i + group) * kTile + t) * 4 + slot: one 8-byte access
+//         moves a group (a warp: 256 contiguous bytes), and each 4-byte half
+//         holds two values of one type, converted by one packed instruction.
+// The offsets of a pixel's values are compile-time constants from one base
+// address, and a tile's whole state is one contiguous block that a single
+// bulk copy moves. The List-1 byte of a pixel lives in a separate byte array
+// indexed by p (n_tiles * kTile bytes).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -31,6 +37,20 @@ constexpr int kStageInputs = 1;   // CamView.flags: frame bytes staged with the 
 constexpr int kModeAugmented = 2; // CamView.flags: one 4-channel mixture (R, G, B, s*depth)
 constexpr uint32_t kRhoEta = 1u;        // StreamPrm.flags: rho = alpha * eta(x | mu, sigma)
 constexpr uint32_t kVarPerChannel = 2u; // StreamPrm.flags: v is the per-channel variance
+
+// Group and slot of a field in the FP16/BF16 layout.
+__host__ __device__ constexpr int h16_group(int f) {
+    return (f == F_MUB || f == F_VC || f == F_MUD || f == F_VD) ? 1 : 0;
+}
+__host__ __device__ constexpr int h16_slot(int f) {
+    return (f == F_WC || f == F_MUB) ? 0 : (f == F_WD || f == F_VC) ? 1
+                                     : (f == F_MUR || f == F_MUD) ? 2 : 3;
+}
+// Element index, within its tile, of field f of component i at tile pixel t.
+template <int PREC> __host__ __device__ constexpr int tile_elem(int i, int f, int t) {
+    return PREC == 0 ? (kFields * i + f) * kTile + t
+                     : ((2 * i + h16_group(f)) * kTile + t) * 4 + h16_slot(f);
+}
 
 struct StreamPrm {
     float alpha, oma, k2, T, init_var, init_w, v_min;
@@ -132,6 +152,85 @@ template <> struct Storage<1> {
         static_cast<__half *>(b)[o] = __float2half_rn(fminf(v, 65504.0f));
     }
 };
+
+// Packed FP16/BF16 conversions. bfloat16 -> float is exact (the bits move
+// up); float -> bfloat16 rounds to nearest even; float -> float16 rounds to
+// nearest even and saturates at the largest finite value (as Storage<1>).
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+__device__ __forceinline__ float2 f16x2_unpack(uint32_t u) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(&u));
+}
+__device__ __forceinline__ uint32_t bf16x2_pack(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ uint32_t f16x2_pack_sat(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// The eight values of one component at one pixel.
+struct Fields {
+    float wc, mur, mug, mub, vc, wd, mud, vd;
+};
+
+// Load / store component i of the pixel whose tile starts at element tb
+// (tile index * 8M * kTile) and sits at column t of it; e0 = tb + t.
+template <int PREC, int M>
+__device__ __forceinline__ Fields load_fields(const void *pl, int64_t e0, int64_t tb, uint32_t t,
+                                              int i) {
+    Fields f;
+    if constexpr (PREC == 0) {
+        using S = Storage<0>;
+        const int64_t b = e0 + kFields * i * kTile;
+        f.wc = S::ldw(pl, b + F_WC * kTile);
+        f.mur = S::ldv(pl, b + F_MUR * kTile);
+        f.mug = S::ldv(pl, b + F_MUG * kTile);
+        f.mub = S::ldv(pl, b + F_MUB * kTile);
+        f.vc = S::ldv(pl, b + F_VC * kTile);
+        f.wd = S::ldw(pl, b + F_WD * kTile);
+        f.mud = S::ldv(pl, b + F_MUD * kTile);
+        f.vd = S::ldv(pl, b + F_VD * kTile);
+    } else {
+        const uint2 *g = static_cast<const uint2 *>(pl) + (tb >> 2) + t + 2 * i * kTile;
+        const uint2 g0 = g[0], g1 = g[kTile];
+        f.wc = bf16_lo(g0.x);
+        f.wd = bf16_hi(g0.x);
+        const float2 rg = f16x2_unpack(g0.y), bv = f16x2_unpack(g1.x), dv = f16x2_unpack(g1.y);
+        f.mur = rg.x; f.mug = rg.y;
+        f.mub = bv.x; f.vc = bv.y;
+        f.mud = dv.x; f.vd = dv.y;
+    }
+    return f;
+}
+
+// kDepth: also write w_d and v_d (FP32 stores them separately; FP16 always
+// writes them with their group).
+template <int PREC, int M, bool kDepth = true>
+__device__ __forceinline__ void store_fields(void *pl, int64_t e0, int64_t tb, uint32_t t, int i,
+                                             const Fields &f) {
+    if constexpr (PREC == 0) {
+        using S = Storage<0>;
+        const int64_t b = e0 + kFields * i * kTile;
+        S::stw(pl, b + F_WC * kTile, f.wc);
+        S::stv(pl, b + F_MUR * kTile, f.mur);
+        S::stv(pl, b + F_MUG * kTile, f.mug);
+        S::stv(pl, b + F_MUB * kTile, f.mub);
+        S::stv(pl, b + F_VC * kTile, f.vc);
+        if (kDepth)
+            S::stw(pl, b + F_WD * kTile, f.wd);
+        S::stv(pl, b + F_MUD * kTile, f.mud);
+        if (kDepth)
+            S::stv(pl, b + F_VD * kTile, f.vd);
+    } else {
+        uint2 *g = static_cast<uint2 *>(pl) + (tb >> 2) + t + 2 * i * kTile;
+        g[0] = make_uint2(bf16x2_pack(f.wc, f.wd), f16x2_pack_sat(f.mur, f.mug));
+        g[kTile] = make_uint2(f16x2_pack_sat(f.mub, f.vc), f16x2_pack_sat(f.mud, f.vd));
+    }
+}
 
 // ------------------------------------------------------------ mixture step
 template <int D> struct Comp {
@@ -299,7 +398,6 @@ __device__ __forceinline__ uint32_t fuse_list1(int fgc, int fgd, uint32_t fb) {
 // augmentation alternative (options honoured too).
 template <int M, int PREC, bool kSkipSorted, int kVariant>
 __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) {
-    using S = Storage<PREC>;
     const uint32_t p32 = (uint32_t)p;
     const uint32_t row = div_wpr(p32 >> 5, cv);
     const uint32_t x = p32 - row * (uint32_t)cv.w_pad;
@@ -310,8 +408,10 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
                          (float)cv.rgb[3 * q + 2]};
     const uint32_t draw = cv.depth[q];
     const float xd[1] = {(float)draw};
-    // Element of plane 0 for this pixel; plane k lies k * kTile further on.
-    const int64_t e0 = (int64_t)(p32 / kTile) * (kFields * M * kTile) + (p32 % kTile);
+    // First element of the pixel's tile, and the pixel's column in it.
+    const int64_t tb = (int64_t)(p32 / kTile) * (kFields * M * kTile);
+    const uint32_t t = p32 % kTile;
+    const int64_t e0 = tb + t;
     const void *pl = cv.planes;
 
     if (kVariant == 2) {
@@ -334,13 +434,10 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
         } else {
 #pragma unroll
             for (int i = 0; i < M; ++i) {
-                const int64_t b = e0 + kFields * i * kTile;
-                a[i].w = S::ldw(pl, b + F_WC * kTile);
-                a[i].mu[0] = S::ldv(pl, b + F_MUR * kTile);
-                a[i].mu[1] = S::ldv(pl, b + F_MUG * kTile);
-                a[i].mu[2] = S::ldv(pl, b + F_MUB * kTile);
-                a[i].mu[3] = S::ldv(pl, b + F_MUD * kTile);
-                a[i].v = S::ldv(pl, b + F_VC * kTile);
+                const Fields f = load_fields<PREC, M>(pl, e0, tb, t, i);
+                a[i].w = f.wc;
+                a[i].mu[0] = f.mur; a[i].mu[1] = f.mug; a[i].mu[2] = f.mub; a[i].mu[3] = f.mud;
+                a[i].v = f.vc;
             }
             if (draw == 0u)
                 xa[3] = a[0].mu[3];
@@ -349,17 +446,13 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
         void *plw = cv.planes;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            const int64_t b = e0 + kFields * i * kTile;
-            S::stw(plw, b + F_WC * kTile, a[i].w);
-            S::stv(plw, b + F_MUR * kTile, a[i].mu[0]);
-            S::stv(plw, b + F_MUG * kTile, a[i].mu[1]);
-            S::stv(plw, b + F_MUB * kTile, a[i].mu[2]);
-            S::stv(plw, b + F_MUD * kTile, a[i].mu[3]);
-            S::stv(plw, b + F_VC * kTile, a[i].v);
-            if (cv.first) { // the unused depth planes read as zero
-                S::stw(plw, b + F_WD * kTile, 0.f);
-                S::stv(plw, b + F_VD * kTile, 0.f);
-            }
+            // w_d and v_d are unused and read as zero
+            const Fields f = {a[i].w, a[i].mu[0], a[i].mu[1], a[i].mu[2], a[i].v,
+                              0.f,    a[i].mu[3], 0.f};
+            if (PREC != 0 || cv.first)
+                store_fields<PREC, M, true>(plw, e0, tb, t, i, f);
+            else
+                store_fields<PREC, M, false>(plw, e0, tb, t, i, f);
         }
         const uint32_t f = (uint32_t)fg;
         cv.fusion[p] = (uint8_t)f;
@@ -384,15 +477,13 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
         fb = cv.fusion[p];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            const int64_t b = e0 + kFields * i * kTile;
-            c[i].w = S::ldw(pl, b + F_WC * kTile);
-            c[i].mu[0] = S::ldv(pl, b + F_MUR * kTile);
-            c[i].mu[1] = S::ldv(pl, b + F_MUG * kTile);
-            c[i].mu[2] = S::ldv(pl, b + F_MUB * kTile);
-            c[i].v = S::ldv(pl, b + F_VC * kTile);
-            d[i].w = S::ldw(pl, b + F_WD * kTile);
-            d[i].mu[0] = S::ldv(pl, b + F_MUD * kTile);
-            d[i].v = S::ldv(pl, b + F_VD * kTile);
+            const Fields f = load_fields<PREC, M>(pl, e0, tb, t, i);
+            c[i].w = f.wc;
+            c[i].mu[0] = f.mur; c[i].mu[1] = f.mug; c[i].mu[2] = f.mub;
+            c[i].v = f.vc;
+            d[i].w = f.wd;
+            d[i].mu[0] = f.mud;
+            d[i].v = f.vd;
         }
         fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0)>(c, xc, cv.pc);
     }
@@ -416,15 +507,9 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
     void *plw = cv.planes;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-        const int64_t b = e0 + kFields * i * kTile;
-        S::stw(plw, b + F_WC * kTile, c[i].w);
-        S::stv(plw, b + F_MUR * kTile, c[i].mu[0]);
-        S::stv(plw, b + F_MUG * kTile, c[i].mu[1]);
-        S::stv(plw, b + F_MUB * kTile, c[i].mu[2]);
-        S::stv(plw, b + F_VC * kTile, c[i].v);
-        S::stw(plw, b + F_WD * kTile, d[i].w);
-        S::stv(plw, b + F_MUD * kTile, d[i].mu[0]);
-        S::stv(plw, b + F_VD * kTile, d[i].v);
+        const Fields f = {c[i].w, c[i].mu[0], c[i].mu[1], c[i].mu[2], c[i].v,
+                          d[i].w, d[i].mu[0], d[i].v};
+        store_fields<PREC, M>(plw, e0, tb, t, i, f);
     }
     cv.fusion[p] = (uint8_t)fb;
     return (fb & 1u) | ((uint32_t)fgc << 1) | ((uint32_t)fgd << 2);

@@ -18,6 +18,11 @@ cudaError_t launch_tick(const gmmdev::CamView &cv, int threads, cudaStream_t s);
 cudaError_t launch_tick_staged(const gmmdev::CamView &cv, int variant, int ctas_per_sm,
                                int *status, cudaStream_t s);
 
+// Bounded-wait self-test (see gmm_wait_selftest): *status gets bit 0 when
+// the wait ran out; *waited_ns the time waited.
+cudaError_t launch_wait_selftest(int *status, unsigned long long *waited_ns,
+                                 unsigned long long limit_ns, cudaStream_t s);
+
 // Byte mask -> bit-packed mask; confusion counts {TP, FP, FN, TN} of two
 // bit-packed masks into out (zeroed first).
 cudaError_t launch_pack(const uint8_t *in, uint32_t *out, int H, int W, cudaStream_t s);

@@ -41,19 +41,25 @@ template <int TP> struct Smem<0, TP> {
         reinterpret_cast<float *>(st + k * TP * 4)[t] = v;
     }
 };
+// FP16/BF16: plane k = 8 i + f is slot h16_slot(f) of group h16_group(f) of
+// component i (the layout of gmm_device.cuh; TP pixels per tile).
 template <int TP> struct Smem<1, TP> {
     static constexpr int kBytes = 2;
+    static __device__ __forceinline__ int at(int k, int t) {
+        const int f = k & 7;
+        return ((2 * (k >> 3) + h16_group(f)) * TP + t) * 4 + h16_slot(f);
+    }
     static __device__ __forceinline__ float ldw(const uint8_t *st, int k, int t) {
-        return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(st + k * TP * 2)[t]);
+        return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(st)[at(k, t)]);
     }
     static __device__ __forceinline__ float ldv(const uint8_t *st, int k, int t) {
-        return __half2float(reinterpret_cast<const __half *>(st + k * TP * 2)[t]);
+        return __half2float(reinterpret_cast<const __half *>(st)[at(k, t)]);
     }
     static __device__ __forceinline__ void stw(uint8_t *st, int k, int t, float v) {
-        reinterpret_cast<__nv_bfloat16 *>(st + k * TP * 2)[t] = __float2bfloat16_rn(v);
+        reinterpret_cast<__nv_bfloat16 *>(st)[at(k, t)] = __float2bfloat16_rn(v);
     }
     static __device__ __forceinline__ void stv(uint8_t *st, int k, int t, float v) {
-        reinterpret_cast<__half *>(st + k * TP * 2)[t] = __float2half_rn(fminf(v, 65504.0f));
+        reinterpret_cast<__half *>(st)[at(k, t)] = __float2half_rn(fminf(v, 65504.0f));
     }
 };
 
@@ -396,6 +402,32 @@ cudaError_t launch_staged_p(const CamView &cv, int ctas, int *status, cudaStream
 } // namespace
 
 namespace gmmhost {
+
+// Self-test of the bounded wait: one thread waits on an mbarrier whose
+// phase can never complete (it expects 16 bytes that no copy delivers). The
+// wait must give up after limit_ns, set bit 0 of *status, record how long it
+// waited, and the kernel must return normally.
+__global__ void k_wait_selftest(int *status, unsigned long long *waited_ns,
+                                unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0)
+        return;
+    gmmtma::mbar_init(&bar, 1);
+    gmmtma::fence_mbar_init();
+    gmmtma::mbar_arrive_expect_tx(&bar, 16);
+    const uint64_t t0 = gmmtma::global_ns();
+    const bool ok = gmmtma::mbar_wait(&bar, 0, limit_ns);
+    *waited_ns = gmmtma::global_ns() - t0;
+    if (!ok)
+        atomicOr(status, 1);
+    gmmtma::mbar_inval(&bar);
+}
+
+cudaError_t launch_wait_selftest(int *status, unsigned long long *waited_ns,
+                                 unsigned long long limit_ns, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(status, waited_ns, limit_ns);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tick_staged(const CamView &cv_in, int variant, int ctas_per_sm, int *status,
                                cudaStream_t s) {

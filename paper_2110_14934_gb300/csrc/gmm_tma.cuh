@@ -43,20 +43,25 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait for the barrier phase with the given parity, for at most about one
-// second of wall time (each try_wait may itself suspend the thread for a
-// hardware-defined interval, so the bound is on time, not on iterations).
-// Returns false if it ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for the barrier phase with the given parity, for at most limit_ns of
+// wall time (default about one second; each try_wait may itself suspend the
+// thread for a hardware-defined interval, so the bound is on time, not on
+// iterations). Returns false if it ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          uint64_t limit_ns = 1000000000ull) {
     if (mbar_try_wait(bar, parity))
         return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         if (mbar_try_wait(bar, parity))
             return true;
-        if (global_ns() - t0 > 1000000000ull)
+        if (global_ns() - t0 > limit_ns)
             return false;
     }
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // Global -> shared bulk copy completing `bytes` of transaction count on bar.

@@ -141,3 +141,22 @@ def test_device_generator_matches_host():
         assert np.array_equal(rd.cpu().numpy(), rgb)
         assert np.array_equal(dd.cpu().numpy().view(np.uint16), dep)
         assert np.array_equal(gd.cpu().numpy(), gt)
+
+
+def test_bounded_wait_runs_out_and_reports():
+    """Failure detection without a GPU fault: a device wait on a barrier that
+    nothing completes (the same time-bounded wait the staged kernel's
+    pipeline uses) gives up after its limit, the kernel reports it and
+    returns, and the context keeps working."""
+    import torch
+    for ms in (50, 300):
+        r = G.wait_selftest(ms)
+        assert r["timed_out"], r
+        assert ms <= r["waited_ms"] < ms + 500, r
+    g = G.GMM(45, 83, 3)
+    rgb, depth, _ = scene_frames(3, 45, 83, 0, 0, 2)
+    for t in range(2):
+        r_, d_ = to_dev(rgb[t], depth[t])
+        g.apply(r_, d_)
+    torch.cuda.synchronize()
+    g.sync()

@@ -40,8 +40,15 @@ def _caller_plane(state, H, W, M, prec, comp, field):
         flat = state.view(torch.bfloat16)
     else:
         flat = state.view(torch.float16)
-    tiles = flat[:n_tiles * 8 * M * 256].reshape(n_tiles, 8 * M, 256)
-    plane = tiles[:, 8 * comp + field, :].reshape(-1)[:H * w_pad]
+    if prec == G.PREC_F32:
+        tiles = flat[:n_tiles * 8 * M * 256].reshape(n_tiles, 8 * M, 256)
+        plane = tiles[:, 8 * comp + field, :].reshape(-1)[:H * w_pad]
+    else:
+        group, slot = {G.PLANE_W_C: (0, 0), G.PLANE_W_D: (0, 1), G.PLANE_MU_R: (0, 2),
+                       G.PLANE_MU_G: (0, 3), G.PLANE_MU_B: (1, 0), G.PLANE_V_C: (1, 1),
+                       G.PLANE_MU_D: (1, 2), G.PLANE_V_D: (1, 3)}[field]
+        tiles = flat[:n_tiles * 8 * M * 256].reshape(n_tiles, 2 * M, 256, 4)
+        plane = tiles[:, 2 * comp + group, :, slot].reshape(-1)[:H * w_pad]
     return plane.float().reshape(H, w_pad)[:, :W].cpu().numpy()
 
 
@@ -79,3 +86,32 @@ def test_noalloc_rejects_frames_above_the_scratch_limit():
     rc = L.gmm_apply_open3_noalloc(ctypes.byref(cfg), None, 1, None, None, None, None)
     assert rc == G.EINVAL
     assert "GMM_NOALLOC_MAX_MASK_WORDS" in L.gmm_last_error().decode()
+
+
+@pytest.mark.parametrize("H,W,M,prec", [(1, 33, 5, G.PREC_F16), (33, 1, 4, G.PREC_F32),
+                                        (7, 1000, 3, G.PREC_F16)])
+def test_noalloc_state_and_mask_stay_in_bounds(H, W, M, prec):
+    """The caller-owned state and the mask sit between canary bytes: three
+    calls at ragged sizes leave the canaries intact."""
+    import torch
+    L = G.load_library()
+    guard, canary = 4096, 0xA5
+    nbytes = G.state_bytes(H, W, M, prec)
+    sbuf = torch.full((guard + nbytes + guard,), canary, dtype=torch.uint8, device="cuda")
+    state = sbuf[guard:guard + nbytes]
+    mwords = H * G.mask_words_per_row(W)
+    mbuf = torch.full((guard + 4 * mwords + guard,), canary, dtype=torch.uint8, device="cuda")
+    mask = mbuf[guard:guard + 4 * mwords]
+    cfg = _config(L, H, W, M, prec)
+    rgb, depth, _ = scene_frames(5 + H, H, W, 1, 0, 3)
+    stream = torch.cuda.current_stream()
+    for t in range(3):
+        r, d = to_dev(rgb[t], depth[t])
+        rc = L.gmm_apply_open3_noalloc(ctypes.byref(cfg), state.data_ptr(), 1 if t == 0 else 0,
+                                       r.data_ptr(), d.data_ptr(), mask.data_ptr(),
+                                       stream.cuda_stream)
+        assert rc == G.OK, L.gmm_last_error()
+    torch.cuda.synchronize()
+    for buf, n in ((sbuf, nbytes), (mbuf, 4 * mwords)):
+        b = buf.cpu().numpy()
+        assert (b[:guard] == canary).all() and (b[guard + n:] == canary).all()

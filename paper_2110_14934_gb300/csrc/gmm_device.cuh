@@ -475,17 +475,42 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
         fgc = 0;
     } else {
         fb = cv.fusion[p];
+        if constexpr (PREC == 0) {
 #pragma unroll
-        for (int i = 0; i < M; ++i) {
-            const Fields f = load_fields<PREC, M>(pl, e0, tb, t, i);
-            c[i].w = f.wc;
-            c[i].mu[0] = f.mur; c[i].mu[1] = f.mug; c[i].mu[2] = f.mub;
-            c[i].v = f.vc;
-            d[i].w = f.wd;
-            d[i].mu[0] = f.mud;
-            d[i].v = f.vd;
+            for (int i = 0; i < M; ++i) {
+                const Fields f = load_fields<PREC, M>(pl, e0, tb, t, i);
+                c[i].w = f.wc;
+                c[i].mu[0] = f.mur; c[i].mu[1] = f.mug; c[i].mu[2] = f.mub;
+                c[i].v = f.vc;
+                d[i].w = f.wd;
+                d[i].mu[0] = f.mud;
+                d[i].v = f.vd;
+            }
+            fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0)>(c, xc, cv.pc);
+        } else {
+            // The depth values stay packed (two registers per component
+            // instead of three) while the colour mixture runs.
+            uint32_t dw[M], dmv[M];
+            const uint2 *g = static_cast<const uint2 *>(pl) + (tb >> 2) + t;
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                const uint2 g0 = g[2 * i * kTile], g1 = g[(2 * i + 1) * kTile];
+                c[i].w = bf16_lo(g0.x);
+                const float2 rg = f16x2_unpack(g0.y), bv = f16x2_unpack(g1.x);
+                c[i].mu[0] = rg.x; c[i].mu[1] = rg.y; c[i].mu[2] = bv.x;
+                c[i].v = bv.y;
+                dw[i] = g0.x;
+                dmv[i] = g1.y;
+            }
+            fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0)>(c, xc, cv.pc);
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                d[i].w = bf16_hi(dw[i]);
+                const float2 mv = f16x2_unpack(dmv[i]);
+                d[i].mu[0] = mv.x;
+                d[i].v = mv.y;
+            }
         }
-        fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0)>(c, xc, cv.pc);
     }
 
     if (draw == 0u) {

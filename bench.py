@@ -615,11 +615,26 @@ def run_pool(args, wl):
                          [b + f * s for b, s in zip(dep_base, dep_step)], mask_ptr)
 
     submit(0)
-    shape = pool.autotune(iters=3) if not args.no_autotune else None
     pool.tick(stream)  # frame 0 initialises every model
-    for k in range(1, Wm):
-        submit(k % nf)
+    k = 1
+    if not args.no_autotune:
+        # online tuning: the first warm-up ticks of the sequence try each
+        # candidate launch shape (3 ticks each) and the pool keeps the best
+        pool.autotune_online(3)
+        while pool.tuning()[0] and k < 2000:
+            submit(k % nf)
+            pool.tick(stream)
+            k += 1
+        torch.cuda.synchronize()
+        tuning, shape = pool.tuning()
+        assert not tuning, "online tuning did not finish"
+        shape["tuning_ticks"] = k - 1
+    else:
+        shape = None
+    for j in range(Wm):
+        submit((k + j) % nf)
         pool.tick(stream)
+    F0 = k + Wm  # frames consumed before the timed region
     torch.cuda.synchronize()
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
@@ -631,7 +646,7 @@ def run_pool(args, wl):
         clocks.start()
     t0.record(stream)
     for k in range(K):
-        submit((Wm + k) % nf)
+        submit((F0 + k) % nf)
         pool.tick(stream)
     t1.record(stream)
     torch.cuda.synchronize()
@@ -651,7 +666,7 @@ def run_pool(args, wl):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(n_lat)]
     for k in range(n_lat):
-        submit((Wm + K + k) % nf)
+        submit((F0 + K + k) % nf)
         ev[k][0].record(stream)
         pool.tick(stream)
         ev[k][1].record(stream)

@@ -163,10 +163,14 @@ int gmm_wait_selftest(int timeout_ms, int *timed_out, double *waited_ms);
 /* Tick kernel of the handle (§IV: the per-pixel GPU pass). Both compute the
  * same arithmetic bit for bit. GMM_KERNEL_DIRECT (default): one thread per
  * pixel, coalesced loads and stores straight from and to HBM (always used
- * for the initialising tick). GMM_KERNEL_STAGED: persistent CTAs stream
- * tiles of the state through shared memory with bulk copies in a
- * multi-stage pipeline; variant picks the depth (0..3: 2..5 stages of one
- * 256-pixel tile each), ctas_per_sm the residency (0 = as many as fit). A staged pipeline wait that runs out is reported by
+ * for the initialising tick); variant picks the CTA size (0, the default:
+ * the measured best for the precision, 128 threads for FP32 and 32 for
+ * FP16/BF16; 1..4: 256, 128, 64, 32 threads), ctas_per_sm is ignored.
+ * GMM_KERNEL_STAGED: persistent CTAs stream tiles of the state through
+ * shared memory with bulk copies in a multi-stage pipeline; variant picks
+ * the depth (0..3: 2..5 stages of one 256-pixel tile each), ctas_per_sm the
+ * residency (0 = as many as fit); the augmentation mode always uses the
+ * direct kernel. A staged pipeline wait that runs out is reported by
  * gmm_sync as GMM_ETIMEOUT. */
 #define GMM_KERNEL_STAGED 0
 #define GMM_KERNEL_DIRECT 1
@@ -363,6 +367,21 @@ int gmm_pool_set_launch(gmm_pool_t *p, int threads, int ctas_per_sm,
  * NULL. Synchronous. */
 int gmm_pool_autotune(gmm_pool_t *p, int iters, int *threads,
                       int *ctas_per_sm, int *tile_pixels);
+
+/* Online tuning of the launch shape on real ticks: the next
+ * ticks_per_shape x (number of candidates) calls of gmm_pool_tick each run
+ * one candidate shape (block size 64/128/256, full or half residency, tiles
+ * of 2048/8192/32768 pixels; round-robin, CUDA graphs off meanwhile), timed
+ * by events on the pool's stream; once all have completed, the shape with
+ * the lowest median tick time is kept and graph use restored. The ticks do
+ * their normal work, so nothing is snapshotted. gmm_pool_set_launch during
+ * tuning is overridden. */
+int gmm_pool_autotune_online(gmm_pool_t *p, int ticks_per_shape);
+
+/* Polls online tuning (non-blocking). Returns 1 while it is still running,
+ * 0 when done (or never started), < 0 on error; writes the current shape to
+ * the non-NULL outputs. */
+int gmm_pool_tuning(gmm_pool_t *p, int *threads, int *ctas_per_sm, int *tile_pixels);
 
 /* Capture the pool's tick in a CUDA graph (enable = 1) and replay it while
  * the set of submitted cameras and their buffers is unchanged. */

@@ -112,6 +112,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_pool_set_stream": (ctypes.c_int, [_vp, _vp]),
         "gmm_pool_set_launch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "gmm_pool_autotune": (ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3),
+        "gmm_pool_autotune_online": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "gmm_pool_tuning": (ctypes.c_int, [_vp] + [ctypes.POINTER(ctypes.c_int)] * 3),
         "gmm_pool_use_graph": (ctypes.c_int, [_vp, ctypes.c_int]),
         "gmm_pool_state_get": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                               ctypes.c_size_t]),
@@ -381,6 +383,17 @@ class Pool:
         _check(load_library().gmm_pool_autotune(self._p, iters, ctypes.byref(t), ctypes.byref(c),
                                                 ctypes.byref(p)))
         return {"threads": t.value, "ctas_per_sm": c.value, "tile_pixels": p.value}
+
+    def autotune_online(self, ticks_per_shape=3) -> None:
+        """Arm online tuning: the next ticks try the candidate shapes in turn."""
+        _check(load_library().gmm_pool_autotune_online(self._p, int(ticks_per_shape)))
+
+    def tuning(self):
+        """(still tuning?, current shape dict)."""
+        t, c, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        rc = _check(load_library().gmm_pool_tuning(self._p, ctypes.byref(t), ctypes.byref(c),
+                                                   ctypes.byref(p)))
+        return bool(rc), {"threads": t.value, "ctas_per_sm": c.value, "tile_pixels": p.value}
 
     def use_graph(self, enable=True) -> None:
         _check(load_library().gmm_pool_use_graph(self._p, int(bool(enable))))

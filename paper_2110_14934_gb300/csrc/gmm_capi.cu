@@ -374,7 +374,10 @@ static int launch_apply(gmm_ctx *h, const uint8_t *rgb, const uint16_t *depth, u
     if (h->initialized && h->kernel == GMM_KERNEL_STAGED && h->cfg.mode == GMM_MODE_FUSION)
         e = gmmhost::launch_tick_staged(v, h->variant, h->ctas_per_sm, h->d_status, h->stream);
     else
-        e = gmmhost::launch_tick(v, 256, h->stream);
+        e = gmmhost::launch_tick(
+            v, gmmhost::direct_threads(h->kernel == GMM_KERNEL_DIRECT ? h->variant : 0,
+                                       h->cfg.precision),
+            h->stream);
     if (e == cudaSuccess && h->cfg.morph_open)
         e = gmmhost::launch_morph_open3(h->morph_tmp, mask, h->cfg.H, h->cfg.W, h->stream);
     if (e != cudaSuccess)
@@ -677,8 +680,9 @@ int gmm_set_kernel(gmm_t *h, int kind, int variant, int ctas_per_sm) {
         return fail(GMM_EINVAL, "gmm_set_kernel: null handle");
     if (kind != GMM_KERNEL_STAGED && kind != GMM_KERNEL_DIRECT)
         return fail(GMM_EINVAL, "gmm_set_kernel: unknown kernel kind");
-    if (variant < 0 || variant > 3)
-        return fail(GMM_EINVAL, "gmm_set_kernel: variant must be in [0, 3]");
+    if (variant < 0 || variant > (kind == GMM_KERNEL_DIRECT ? 4 : 3))
+        return fail(GMM_EINVAL, "gmm_set_kernel: variant must be in [0, 4] (direct) or [0, 3] "
+                                "(staged)");
     if (ctas_per_sm < 0 || ctas_per_sm > 32)
         return fail(GMM_EINVAL, "gmm_set_kernel: ctas_per_sm must be in [0, 32]");
     h->kernel = kind;

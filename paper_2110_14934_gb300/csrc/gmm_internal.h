@@ -8,8 +8,23 @@
 
 namespace gmmhost {
 
-// Single-camera tick: one thread per padded pixel. threads: block size.
+// Single-camera tick: one thread per padded pixel. threads: block size (32,
+// 64, 128 or 256).
 cudaError_t launch_tick(const gmmdev::CamView &cv, int threads, cudaStream_t s);
+
+// Block size of the direct tick kernel for gmm_set_kernel's variant: 0 the
+// measured best for the storage precision (FP32: 128, FP16/BF16: 32, one warp
+// per CTA, so a finished warp's slot is refilled at once), 1..4: 256, 128,
+// 64, 32.
+inline int direct_threads(int variant, int prec) {
+    switch (variant) {
+    case 1: return 256;
+    case 2: return 128;
+    case 3: return 64;
+    case 4: return 32;
+    default: return prec == 0 ? 128 : 32;
+    }
+}
 
 // Staged single-camera tick (bulk-copy pipeline through shared memory).
 // variant: pipeline depth (0..3: 2..5 stages of one 256-pixel tile);

@@ -17,19 +17,23 @@ using gmmhost::PoolArgs;
 namespace {
 
 // ------------------------------------------------------------ single camera
+// One thread per padded pixel (n_pad is a multiple of 32: whole warps leave).
 template <int M, int PREC, int V>
 __device__ __forceinline__ void tick_body(const CamView &cv) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= cv.n_pad) // n_pad is a multiple of 32: whole warps leave
+    if (p >= cv.n_pad)
         return;
     const uint32_t bits = process_pixel<M, PREC, PREC != 0, V>(cv, p);
     write_mask_words(cv, p >> 5, bits);
 }
 
 // FP32 state: HBM-bound; the register allocation without a residency hint
-// (64 registers, 4 CTAs per SM) measured fastest. FP16/BF16 state: issue
-// bound; at least 4 CTAs per SM. V: process_pixel's variant (the options
-// are separate instantiations, so the default kernels carry none of them).
+// (64 registers) measured fastest. FP16/BF16 state: issue bound; at least
+// 1024 threads per SM. V: process_pixel's variant (the options are separate
+// instantiations, so the default kernels carry none of them). Small CTAs
+// (128 threads) measured faster than 256: a CTA's slot frees as soon as its
+// own 4 warps finish. A persistent grid-stride form measured slower (its loop
+// costs registers: 66 in FP32, i.e. 3 CTAs of 256 per SM).
 template <int M, int V>
 __global__ void __launch_bounds__(256) k_tick_f32(const CamView cv) { tick_body<M, 0, V>(cv); }
 template <int M, int V>
@@ -273,6 +277,8 @@ namespace gmmhost {
 cudaError_t launch_tick(const CamView &cv, int threads, cudaStream_t s) {
     if (cv.n_pad == 0)
         return cudaSuccess;
+    if (threads != 32 && threads != 64 && threads != 128 && threads != 256)
+        return cudaErrorInvalidValue;
     if (cv.prec == 0) {
         switch (cv.M) {
         case 3: return launch_tick_t<3, 0>(cv, threads, s);

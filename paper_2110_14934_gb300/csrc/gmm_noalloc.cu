@@ -78,7 +78,7 @@ extern "C" int gmm_apply_open3_noalloc(const gmm_config *cfg, void *state, int f
     const gmmdev::CamView v = make_view(*cfg, L, state, rgb8, depth16, scratch, nullptr,
                                         nullptr, first);
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = gmmhost::launch_tick(v, 256, s);
+    cudaError_t e = gmmhost::launch_tick(v, gmmhost::direct_threads(0, cfg->precision), s);
     if (e == cudaSuccess)
         e = gmmhost::launch_morph_open3(scratch, mask_out, cfg->H, cfg->W, s);
     if (e != cudaSuccess)

@@ -43,6 +43,26 @@ struct GraphSig {
 
 constexpr int kStaging = 2;
 
+struct Shape {
+    int threads, ctas, tile;
+};
+
+// Online tuning: real ticks cycle through candidate launch shapes, each tick
+// timed by an event pair on the pool's stream; when every candidate has run
+// its ticks, the shape with the lowest median tick time is kept.
+struct Trial {
+    int cand;
+    cudaEvent_t a, b;
+};
+struct Tuning {
+    bool active = false;
+    bool saved_graph = false;
+    int per_shape = 0, issued = 0;
+    std::vector<Shape> cands;
+    std::vector<Trial> pending;
+    std::vector<std::vector<float>> ms;
+};
+
 } // namespace
 
 namespace gmmhost {
@@ -56,7 +76,7 @@ struct gmm_pool {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr; // graph capture (the legacy stream cannot capture)
     cudaError_t sticky = cudaSuccess;
-    int threads = 256, ctas_per_sm = 0, tile_pixels = 4096;
+    int threads = 128, ctas_per_sm = 0, tile_pixels = 2048;
     CamView *d_views = nullptr;
     int64_t *d_tile_begin = nullptr;
     int *d_counter = nullptr;
@@ -68,6 +88,7 @@ struct gmm_pool {
     bool use_graph = false;
     cudaGraphExec_t gexec[kStaging] = {};
     GraphSig gsig[kStaging];
+    Tuning tune;
 };
 
 static void destroy_graphs(gmm_pool *p) {
@@ -111,6 +132,72 @@ static cudaError_t enqueue_body(gmm_pool *p, cudaStream_t s, int b, int n_jobs, 
     return gmmhost::launch_pool_tick_impl(a, p->threads, blocks, p->prec, all_variants, s);
 }
 
+// Candidate launch shapes: block sizes, full or half residency, tile sizes.
+static std::vector<Shape> tuning_candidates(const gmm_pool *p) {
+    std::vector<Shape> out;
+    const int cand_threads[] = {64, 128, 256};
+    const int cand_tiles[] = {2048, 8192, 32768};
+    for (int t : cand_threads) {
+        const int max_c = gmmhost::pool_max_ctas_per_sm(p->prec, t);
+        const int cand_c[2] = {max_c, max_c > 1 ? max_c / 2 : 0};
+        for (int c : cand_c)
+            if (c >= 1)
+                for (int tp : cand_tiles)
+                    out.push_back({t, c, tp});
+    }
+    return out;
+}
+
+static float median(std::vector<float> v) {
+    if (v.empty())
+        return -1.f;
+    std::sort(v.begin(), v.end());
+    return v[v.size() / 2];
+}
+
+// Read the finished trials; when all are in, keep the best shape.
+static int tuning_poll(gmm_pool *p, bool block) {
+    Tuning &tu = p->tune;
+    if (!tu.active)
+        return GMM_OK;
+    size_t k = 0;
+    for (; k < tu.pending.size(); ++k) {
+        Trial &tr = tu.pending[k];
+        cudaError_t e = block ? cudaEventSynchronize(tr.b) : cudaEventQuery(tr.b);
+        if (e == cudaErrorNotReady)
+            break;
+        float ms = 0.f;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, tr.a, tr.b);
+        cudaEventDestroy(tr.a);
+        cudaEventDestroy(tr.b);
+        if (e != cudaSuccess) {
+            tu.pending.erase(tu.pending.begin(), tu.pending.begin() + (long)k + 1);
+            return cuda_fail(&p->sticky, e, "gmm_pool tuning");
+        }
+        tu.ms[tr.cand].push_back(ms);
+    }
+    tu.pending.erase(tu.pending.begin(), tu.pending.begin() + (long)k);
+    const int total = (int)tu.cands.size() * tu.per_shape;
+    if (tu.issued < total || !tu.pending.empty())
+        return GMM_OK;
+    int best = 0;
+    float best_ms = -1.f;
+    for (size_t c = 0; c < tu.cands.size(); ++c) {
+        const float m = median(tu.ms[c]);
+        if (m >= 0.f && (best_ms < 0.f || m < best_ms)) {
+            best_ms = m;
+            best = (int)c;
+        }
+    }
+    p->threads = tu.cands[best].threads;
+    p->ctas_per_sm = tu.cands[best].ctas;
+    p->tile_pixels = tu.cands[best].tile;
+    p->use_graph = tu.saved_graph;
+    tu.active = false;
+    return GMM_OK;
+}
+
 // One tick over the submitted cameras. clear: drop the submissions and mark
 // the cameras initialised afterwards (false while autotuning).
 static int pool_tick_impl(gmm_pool *p, bool clear) {
@@ -126,6 +213,18 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         if (rc != GMM_OK)
             return rc;
     }
+    // An online-tuning trial sets its launch shape first: the tile table
+    // below depends on the tile size.
+    Tuning &tu = p->tune;
+    const bool trial = clear && tu.active && tu.issued < (int)tu.cands.size() * tu.per_shape;
+    Trial tr{};
+    if (trial) {
+        // round-robin over the candidates, so drift in the frames spreads evenly
+        tr.cand = tu.issued % (int)tu.cands.size();
+        p->threads = tu.cands[tr.cand].threads;
+        p->ctas_per_sm = tu.cands[tr.cand].ctas;
+        p->tile_pixels = tu.cands[tr.cand].tile;
+    }
     int j = 0;
     int64_t tiles = 0;
     bool all_variants = false; // some camera needs the options or the augmented mixture
@@ -140,8 +239,17 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         ++j;
     }
     p->h_tile_begin[b][n_jobs] = tiles;
-    const int blocks = blocks_for(p);
     cudaError_t e = cudaSuccess;
+    if (trial) {
+        e = cudaEventCreate(&tr.a);
+        if (e == cudaSuccess)
+            e = cudaEventCreate(&tr.b);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(tr.a, p->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(&p->sticky, e, "gmm_pool_tick tuning");
+    }
+    const int blocks = blocks_for(p);
     if (p->use_graph) {
         GraphSig sig;
         sig.n_jobs = n_jobs;
@@ -175,6 +283,13 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
     } else {
         e = enqueue_body(p, p->stream, b, n_jobs, tiles, blocks, all_variants);
     }
+    if (e == cudaSuccess && trial) {
+        e = cudaEventRecord(tr.b, p->stream);
+        if (e == cudaSuccess) {
+            tu.pending.push_back(tr);
+            ++tu.issued;
+        }
+    }
     if (e == cudaSuccess)
         e = cudaEventRecord(p->ev_staged[b], p->stream);
     if (e != cudaSuccess)
@@ -189,7 +304,7 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
             }
         }
     }
-    return GMM_OK;
+    return tuning_poll(p, false);
 }
 
 static bool valid_cam(const gmm_pool *p, int cam) {
@@ -371,10 +486,50 @@ int gmm_pool_set_launch(gmm_pool_t *p, int threads, int ctas_per_sm, int tile_pi
 int gmm_pool_use_graph(gmm_pool_t *p, int enable) {
     if (!p)
         return fail(GMM_EINVAL, "gmm_pool_use_graph: null pool");
+    if (p->tune.active) { // applies once online tuning has finished
+        p->tune.saved_graph = enable != 0;
+        return GMM_OK;
+    }
     p->use_graph = enable != 0;
     if (!p->use_graph)
         destroy_graphs(p);
     return GMM_OK;
+}
+
+int gmm_pool_autotune_online(gmm_pool_t *p, int ticks_per_shape) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_autotune_online: null pool");
+    if (ticks_per_shape < 1 || ticks_per_shape > 1000)
+        return fail(GMM_EINVAL, "gmm_pool_autotune_online: ticks_per_shape must be in [1, 1000]");
+    DeviceGuard g(p->device);
+    const int rc = tuning_poll(p, true); // finish an earlier run first
+    if (rc != GMM_OK)
+        return rc;
+    Tuning &tu = p->tune;
+    tu.cands = tuning_candidates(p);
+    tu.ms.assign(tu.cands.size(), {});
+    tu.per_shape = ticks_per_shape;
+    tu.issued = 0;
+    tu.saved_graph = p->use_graph;
+    p->use_graph = false; // each trial tick launches directly
+    tu.active = true;
+    return GMM_OK;
+}
+
+int gmm_pool_tuning(gmm_pool_t *p, int *threads, int *ctas_per_sm, int *tile_pixels) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_tuning: null pool");
+    DeviceGuard g(p->device);
+    const int rc = tuning_poll(p, false);
+    if (rc != GMM_OK)
+        return rc;
+    if (threads)
+        *threads = p->threads;
+    if (ctas_per_sm)
+        *ctas_per_sm = p->ctas_per_sm;
+    if (tile_pixels)
+        *tile_pixels = p->tile_pixels;
+    return p->tune.active ? 1 : 0;
 }
 
 int gmm_pool_autotune(gmm_pool_t *p, int iters, int *threads_out, int *ctas_out,
@@ -422,44 +577,39 @@ int gmm_pool_autotune(gmm_pool_t *p, int iters, int *threads_out, int *ctas_out,
     p->use_graph = false;
     int best_t = saved_t, best_c = saved_c, best_tp = saved_tp;
     float best_ms = -1.f;
-    const int cand_threads[] = {128, 256};
-    const int cand_tiles[] = {2048, 8192, 32768};
+    const std::vector<Shape> cands = tuning_candidates(p);
     int rc = GMM_OK;
-    for (int t : cand_threads) {
-        const int max_c = gmmhost::pool_max_ctas_per_sm(p->prec, t);
-        int cand_c[2] = {max_c, max_c > 1 ? max_c / 2 : 0};
-        for (int c : cand_c) {
-            if (c < 1)
-                continue;
-            for (int tp : cand_tiles) {
-                if (e != cudaSuccess || rc != GMM_OK)
-                    break;
-                p->threads = t;
-                p->ctas_per_sm = c;
-                p->tile_pixels = tp;
-                rc = pool_tick_impl(p, false); // warm-up of this shape
-                if (rc != GMM_OK)
-                    break;
-                e = cudaEventRecord(t0, p->stream);
-                for (int k = 0; k < iters && rc == GMM_OK; ++k)
-                    rc = pool_tick_impl(p, false);
-                if (e == cudaSuccess)
-                    e = cudaEventRecord(t1, p->stream);
-                if (e == cudaSuccess)
-                    e = cudaEventSynchronize(t1);
-                float ms = 0.f;
-                if (e == cudaSuccess)
-                    e = cudaEventElapsedTime(&ms, t0, t1);
-                if (e == cudaSuccess && rc == GMM_OK && (best_ms < 0.f || ms < best_ms)) {
-                    best_ms = ms;
-                    best_t = t;
-                    best_c = c;
-                    best_tp = tp;
-                }
-                for (PoolCam &cam : p->cams)
-                    if (cam.used && cam.submitted)
-                        cam.initialized = 1; // later trials update, as real ticks would
+    // Two passes over the candidates (the best time of each counts), so a
+    // transient slowdown during one trial does not decide the shape.
+    for (int pass = 0; pass < 2; ++pass) {
+        for (const Shape &sh : cands) {
+            if (e != cudaSuccess || rc != GMM_OK)
+                break;
+            p->threads = sh.threads;
+            p->ctas_per_sm = sh.ctas;
+            p->tile_pixels = sh.tile;
+            rc = pool_tick_impl(p, false); // warm-up of this shape
+            if (rc != GMM_OK)
+                break;
+            e = cudaEventRecord(t0, p->stream);
+            for (int k = 0; k < iters && rc == GMM_OK; ++k)
+                rc = pool_tick_impl(p, false);
+            if (e == cudaSuccess)
+                e = cudaEventRecord(t1, p->stream);
+            if (e == cudaSuccess)
+                e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (e == cudaSuccess)
+                e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e == cudaSuccess && rc == GMM_OK && (best_ms < 0.f || ms < best_ms)) {
+                best_ms = ms;
+                best_t = sh.threads;
+                best_c = sh.ctas;
+                best_tp = sh.tile;
             }
+            for (PoolCam &cam : p->cams)
+                if (cam.used && cam.submitted)
+                    cam.initialized = 1; // later trials update, as real ticks would
         }
     }
     // Restore the snapshot and the initialisation flags.
@@ -530,6 +680,11 @@ int gmm_pool_destroy(gmm_pool_t *p) {
     DeviceGuard g(p->device);
     cudaStreamSynchronize(p->stream);
     destroy_graphs(p);
+    for (Trial &tr : p->tune.pending) {
+        cudaEventDestroy(tr.a);
+        cudaEventDestroy(tr.b);
+    }
+    p->tune.pending.clear();
     for (PoolCam &c : p->cams)
         if (c.used && c.arena)
             cudaFreeAsync(c.arena, p->stream);

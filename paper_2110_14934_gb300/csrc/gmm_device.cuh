@@ -305,6 +305,22 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
     const bool matched = j >= 0;
     const int jj = matched ? j : M - 1;
 
+    // The component that changes (matched, or the last-ranked on a miss),
+    // gathered once.
+    float muj[D], vj = c[0].v;
+#pragma unroll
+    for (int ch = 0; ch < D; ++ch)
+        muj[ch] = c[0].mu[ch];
+#pragma unroll
+    for (int i = 1; i < M; ++i) {
+        if (i == jj) {
+            vj = c[i].v;
+#pragma unroll
+            for (int ch = 0; ch < D; ++ch)
+                muj[ch] = c[i].mu[ch];
+        }
+    }
+
     // Weights decay; the matched one gains alpha, or the last-ranked one is
     // replaced on a miss; then renormalise.
     float sum = 0.f;
@@ -317,30 +333,36 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
         sum += w;
     }
     const float inv = 1.0f / sum;
+
+    // Mean and variance of the changed component (the variance from the
+    // squared distance to the new mean).
+    if (matched) {
+        float orho = p.oma, rho = p.alpha;
+        if (kOptions)
+            rho = match_rate<D>(p, d2j, vj, orho);
+        float d2n = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < D; ++ch) {
+            muj[ch] = fmaf(orho, muj[ch], rho * x[ch]);
+            const float df = x[ch] - muj[ch];
+            d2n = fmaf(df, df, d2n);
+        }
+        vj = fmaxf(p.v_min, fmaf(orho, vj, rho * (kOptions ? var_sample<D>(p, d2n) : d2n)));
+    } else {
+#pragma unroll
+        for (int ch = 0; ch < D; ++ch)
+            muj[ch] = x[ch];
+        vj = p.init_var;
+    }
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         c[i].w *= inv;
         c[i].idx = i;
         if (i == jj) {
-            if (matched) {
-                float orho = p.oma, rho = p.alpha;
-                if (kOptions)
-                    rho = match_rate<D>(p, d2j, c[i].v, orho);
-                float d2 = 0.f;
 #pragma unroll
-                for (int ch = 0; ch < D; ++ch) {
-                    const float m = fmaf(orho, c[i].mu[ch], rho * x[ch]);
-                    c[i].mu[ch] = m;
-                    const float df = x[ch] - m;
-                    d2 = fmaf(df, df, d2);
-                }
-                c[i].v = fmaxf(p.v_min, fmaf(orho, c[i].v, rho * (kOptions ? var_sample<D>(p, d2) : d2)));
-            } else {
-#pragma unroll
-                for (int ch = 0; ch < D; ++ch)
-                    c[i].mu[ch] = x[ch];
-                c[i].v = p.init_var;
-            }
+            for (int ch = 0; ch < D; ++ch)
+                c[i].mu[ch] = muj[ch];
+            c[i].v = vj;
         }
         c[i].key = c[i].w * rsqrtf(c[i].v);
     }

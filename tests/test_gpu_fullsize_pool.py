@@ -1,0 +1,153 @@
+"""The many-camera workloads at full size, in the launch configuration the
+bench times: 64 cameras (16 each at 320x240, 640x480, 1280x720, 1920x1080,
+M from {3, 5} by seed) in one pool, CUDA graph requested, launch shape chosen
+by the online tuner during the first ticks. Checked on sampled outputs the
+oracle computes one by one: a band of two full rows per camera (pixels are
+independent, so the oracle runs the band as a 2 x W image).
+
+FP32 state: both sides free-running; a pixel whose FP32 and FP64 decisions
+came within the free-running margin of a threshold is counted as diverged and
+left out afterwards; any other mask difference fails; then the state of one
+camera per resolution and M is checked at the parity tolerance and its last
+tick is teacher-forced at the strict single-step bar.
+FP16/BF16 state: the last tick is teacher-forced (the oracle continues from
+the GPU's stored state) and held to the storage-rounding tolerance."""
+import numpy as np
+import pytest
+
+import bench
+import oracle as O
+import paper_2110_14934_gb300 as G
+import synth
+from parity import FREE_RUN_EPS, state_mismatch, words
+
+pytestmark = pytest.mark.gpu
+
+PRM = dict(alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0, init_w=0.05)
+T = 24          # ticks: the first 18 run the online tuner's candidate shapes
+BAND = 2        # rows per camera checked against the oracle
+
+
+def _setup(prec):
+    import torch
+    cams = bench.camera_mix(16, 0)
+    pool = G.Pool(precision=prec, max_cams=len(cams))
+    ids = [pool.admit(H, W, M, **PRM) for (H, W, M, _) in cams]
+    pool.use_graph(True)
+    pool.autotune_online(1)
+    dev, host = [], []
+    for (H, W, M, seed) in cams:
+        s = synth.scene(seed, H, W, 1)
+        r, d, _ = synth.frames_device(s, 0, T, with_gt=False)
+        dev.append((r, d))
+        y0 = H // 2
+        rh, dh, _ = synth.rows_host(s, 0, T, y0, BAND)
+        host.append((y0, rh, dh))
+    masks = [torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda")
+             for (H, W, _, _) in cams]
+    return cams, pool, ids, dev, host, masks
+
+
+def _tick(pool, ids, dev, masks, t):
+    import torch
+    for i, cam in enumerate(ids):
+        pool.submit(cam, dev[i][0][t], dev[i][1][t], masks[i])
+    pool.tick()
+    torch.cuda.synchronize()
+
+
+def _band(mask, y0, W):
+    """The band's rows of a bit-packed device mask, unpacked."""
+    return G.unpack_mask(words(mask[y0:y0 + BAND]), BAND, W)
+
+
+def _sample_cams(cams):
+    """One camera per (resolution, M) pair present."""
+    seen, out = set(), []
+    for i, (H, W, M, _) in enumerate(cams):
+        if (H, W, M) not in seen:
+            seen.add((H, W, M))
+            out.append(i)
+    return out
+
+
+def test_full_size_pool_fp32():
+    """Free-running for T-1 ticks (masks of every camera's band checked
+    outside diverged pixels), then the last tick teacher-forced for one
+    camera per resolution and M at the strict single-step bar. (Every pixel
+    starts from the same initial weights, so around tick 10 the background
+    prefix sums of most pixels pass T together: many pixels are flagged near
+    a threshold at the free-running margin early in a sequence.)"""
+    cams, pool, ids, dev, host, masks = _setup(G.PREC_F32)
+    orcs = [O.OracleGMM(BAND, W, M, **PRM, eps=FREE_RUN_EPS) for (H, W, M, _) in cams]
+    diverged = [np.zeros((BAND, W), bool) for (H, W, _, _) in cams]
+    for t in range(T - 1):
+        _tick(pool, ids, dev, masks, t)
+        for i, (H, W, M, _) in enumerate(cams):
+            y0, rh, dh = host[i]
+            o = orcs[i].tick(rh[t], dh[t])
+            diverged[i] |= o["near"] != 0
+            g = _band(masks[i], y0, W)
+            bad = (g != o["fused"].astype(bool)) & ~diverged[i]
+            assert not bad.any(), (t, i, (H, W, M), int(bad.sum()))
+    assert not pool.tuning()[0]
+    sample = _sample_cams(cams)
+    tf = {}
+    for i in sample:
+        H, W, M, _ = cams[i]
+        y0 = host[i][0]
+        planes = pool.planes(ids[i])[:, :, y0:y0 + BAND, :].astype(np.float64)
+        fusion = pool.fusion(ids[i])[y0:y0 + BAND]
+        st = state_mismatch(planes, orcs[i].planes(), orcs[i].fusion_bytes(),
+                            exclude=diverged[i])
+        assert sum(st["bad"]) == 0, (i, (H, W, M), st)
+        o = O.OracleGMM(BAND, W, M, **PRM)
+        o.set_state(planes, fusion)
+        tf[i] = o
+    _tick(pool, ids, dev, masks, T - 1)
+    for i in sample:
+        H, W, M, _ = cams[i]
+        y0, rh, dh = host[i]
+        o = tf[i].tick(rh[T - 1], dh[T - 1])
+        exempt = o["near"] != 0
+        bad = (_band(masks[i], y0, W) != o["fused"].astype(bool)) & ~exempt
+        assert not bad.any(), (i, (H, W, M), int(bad.sum()))
+        gp = pool.planes(ids[i])[:, :, y0:y0 + BAND, :]
+        st = state_mismatch(gp, tf[i].planes(), tf[i].fusion_bytes(), exclude=exempt)
+        assert sum(st["bad"]) == 0, (i, (H, W, M), st)
+        assert np.count_nonzero(exempt) < 0.01 * exempt.size
+    pool.close()
+
+
+def test_full_size_pool_fp16_teacher_forced_last_tick():
+    cams, pool, ids, dev, host, masks = _setup(G.PREC_F16)
+    for t in range(T - 1):
+        _tick(pool, ids, dev, masks, t)
+    assert not pool.tuning()[0]
+    sample = _sample_cams(cams)
+    orcs = {}
+    for i in sample:
+        H, W, M, _ = cams[i]
+        y0 = host[i][0]
+        o = O.OracleGMM(BAND, W, M, **PRM)
+        o.set_state(pool.planes(ids[i])[:, :, y0:y0 + BAND, :].astype(np.float64),
+                    pool.fusion(ids[i])[y0:y0 + BAND])
+        orcs[i] = o
+    _tick(pool, ids, dev, masks, T - 1)
+    floors = np.array([1e-3, 1.0, 1.0, 1.0, 1.0, 1e-3, 1.0, 1.0])
+    tol = {0: 2 ** -8, 5: 2 ** -8, 1: 2 ** -11, 2: 2 ** -11, 3: 2 ** -11, 4: 2 ** -11,
+           6: 2 ** -11, 7: 2 ** -11}
+    for i in sample:
+        H, W, M, _ = cams[i]
+        y0, rh, dh = host[i]
+        o = orcs[i].tick(rh[T - 1], dh[T - 1])
+        exempt = o["near"] != 0
+        g = {"fused": _band(masks[i], y0, W)}
+        bad = (g["fused"] != o["fused"].astype(bool)) & ~exempt
+        assert not bad.any(), (i, (H, W, M), int(bad.sum()))
+        gp = pool.planes(ids[i])[:, :, y0:y0 + BAND, :]
+        for f, rt in tol.items():
+            st = state_mismatch(gp, orcs[i].planes(), orcs[i].fusion_bytes(), exclude=exempt,
+                                rtol=rt * 1.01, floors=floors)
+            assert st["bad"][f] == 0, (i, (H, W, M), f, st)
+    pool.close()

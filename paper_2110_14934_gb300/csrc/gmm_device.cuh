@@ -118,44 +118,11 @@ __device__ __forceinline__ uint32_t div_wpr(uint32_t n, const CamView &cv) {
 }
 
 // ------------------------------------------------------------ storage types
-template <int PREC> struct Storage;
-template <> struct Storage<0> {
-    static constexpr int kBytes = 4;
-    static __device__ __forceinline__ float ldw(const void *b, int64_t o) {
-        return static_cast<const float *>(b)[o];
-    }
-    static __device__ __forceinline__ float ldv(const void *b, int64_t o) {
-        return static_cast<const float *>(b)[o];
-    }
-    static __device__ __forceinline__ void stw(void *b, int64_t o, float v) {
-        static_cast<float *>(b)[o] = v;
-    }
-    static __device__ __forceinline__ void stv(void *b, int64_t o, float v) {
-        static_cast<float *>(b)[o] = v;
-    }
-};
-// Means and variances in float16, weights in bfloat16 (weights need range
-// near zero more than mantissa). Values above the float16 range are clamped
-// to its largest finite value instead of becoming infinite.
-template <> struct Storage<1> {
-    static constexpr int kBytes = 2;
-    static __device__ __forceinline__ float ldw(const void *b, int64_t o) {
-        return __bfloat162float(static_cast<const __nv_bfloat16 *>(b)[o]);
-    }
-    static __device__ __forceinline__ float ldv(const void *b, int64_t o) {
-        return __half2float(static_cast<const __half *>(b)[o]);
-    }
-    static __device__ __forceinline__ void stw(void *b, int64_t o, float v) {
-        static_cast<__nv_bfloat16 *>(b)[o] = __float2bfloat16_rn(v);
-    }
-    static __device__ __forceinline__ void stv(void *b, int64_t o, float v) {
-        static_cast<__half *>(b)[o] = __float2half_rn(fminf(v, 65504.0f));
-    }
-};
-
-// Packed FP16/BF16 conversions. bfloat16 -> float is exact (the bits move
-// up); float -> bfloat16 rounds to nearest even; float -> float16 rounds to
-// nearest even and saturates at the largest finite value (as Storage<1>).
+// FP16/BF16 state: means and variances in float16, weights in bfloat16
+// (weights need range near zero more than mantissa), converted in pairs.
+// bfloat16 -> float is exact (the bits move up); float -> bfloat16 rounds to
+// nearest even; float -> float16 rounds to nearest even and saturates at the
+// largest finite value instead of becoming infinite.
 __device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
 __device__ __forceinline__ float2 f16x2_unpack(uint32_t u) {
@@ -184,16 +151,15 @@ __device__ __forceinline__ Fields load_fields(const void *pl, int64_t e0, int64_
                                               int i) {
     Fields f;
     if constexpr (PREC == 0) {
-        using S = Storage<0>;
-        const int64_t b = e0 + kFields * i * kTile;
-        f.wc = S::ldw(pl, b + F_WC * kTile);
-        f.mur = S::ldv(pl, b + F_MUR * kTile);
-        f.mug = S::ldv(pl, b + F_MUG * kTile);
-        f.mub = S::ldv(pl, b + F_MUB * kTile);
-        f.vc = S::ldv(pl, b + F_VC * kTile);
-        f.wd = S::ldw(pl, b + F_WD * kTile);
-        f.mud = S::ldv(pl, b + F_MUD * kTile);
-        f.vd = S::ldv(pl, b + F_VD * kTile);
+        const float *b = static_cast<const float *>(pl) + e0 + kFields * i * kTile;
+        f.wc = b[F_WC * kTile];
+        f.mur = b[F_MUR * kTile];
+        f.mug = b[F_MUG * kTile];
+        f.mub = b[F_MUB * kTile];
+        f.vc = b[F_VC * kTile];
+        f.wd = b[F_WD * kTile];
+        f.mud = b[F_MUD * kTile];
+        f.vd = b[F_VD * kTile];
     } else {
         const uint2 *g = static_cast<const uint2 *>(pl) + (tb >> 2) + t + 2 * i * kTile;
         const uint2 g0 = g[0], g1 = g[kTile];
@@ -213,18 +179,17 @@ template <int PREC, int M, bool kDepth = true>
 __device__ __forceinline__ void store_fields(void *pl, int64_t e0, int64_t tb, uint32_t t, int i,
                                              const Fields &f) {
     if constexpr (PREC == 0) {
-        using S = Storage<0>;
-        const int64_t b = e0 + kFields * i * kTile;
-        S::stw(pl, b + F_WC * kTile, f.wc);
-        S::stv(pl, b + F_MUR * kTile, f.mur);
-        S::stv(pl, b + F_MUG * kTile, f.mug);
-        S::stv(pl, b + F_MUB * kTile, f.mub);
-        S::stv(pl, b + F_VC * kTile, f.vc);
+        float *b = static_cast<float *>(pl) + e0 + kFields * i * kTile;
+        b[F_WC * kTile] = f.wc;
+        b[F_MUR * kTile] = f.mur;
+        b[F_MUG * kTile] = f.mug;
+        b[F_MUB * kTile] = f.mub;
+        b[F_VC * kTile] = f.vc;
         if (kDepth)
-            S::stw(pl, b + F_WD * kTile, f.wd);
-        S::stv(pl, b + F_MUD * kTile, f.mud);
+            b[F_WD * kTile] = f.wd;
+        b[F_MUD * kTile] = f.mud;
         if (kDepth)
-            S::stv(pl, b + F_VD * kTile, f.vd);
+            b[F_VD * kTile] = f.vd;
     } else {
         uint2 *g = static_cast<uint2 *>(pl) + (tb >> 2) + t + 2 * i * kTile;
         g[0] = make_uint2(bf16x2_pack(f.wc, f.wd), f16x2_pack_sat(f.mur, f.mug));

@@ -150,6 +150,14 @@ gmm_t *gmm_create_ex(const gmm_config *cfg);
  * default stream). The caller keeps the stream alive. */
 int gmm_set_stream(gmm_t *h, void *cuda_stream);
 
+/* Failure-path test hook (no counterpart in the paper): records cuda_error
+ * (a nonzero cudaError_t value) as the handle's sticky CUDA failure, exactly
+ * as a failing CUDA call on the handle would, so that the error path can be
+ * exercised without a GPU fault. Every later call that would launch work or
+ * copy returns GMM_ECUDA; the handle can only be destroyed. GMM_EINVAL for a
+ * NULL handle or a zero code. */
+int gmm_inject_cuda_error(gmm_t *h, int cuda_error);
+
 /* Self-test of the bounded device wait the staged kernel relies on (no
  * counterpart in the paper). Launches one thread that waits on a barrier
  * that nothing completes, with the same time-bounded wait; the wait must run
@@ -351,6 +359,9 @@ int gmm_pool_submit_many(gmm_pool_t *p, int n, const int *cams,
 /* Advance every submitted camera by one frame in one launch (asynchronous
  * on the pool's stream), then clear the submissions. */
 int gmm_pool_tick(gmm_pool_t *p);
+
+/* As gmm_inject_cuda_error, for a pool: later ticks return GMM_ECUDA. */
+int gmm_pool_inject_cuda_error(gmm_pool_t *p, int cuda_error);
 
 int gmm_pool_set_stream(gmm_pool_t *p, void *cuda_stream);
 

@@ -83,6 +83,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "gmm_wait_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_double)]),
+        "gmm_inject_cuda_error": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "gmm_pool_inject_cuda_error": (ctypes.c_int, [_vp, ctypes.c_int]),
         "gmm_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         "gmm_apply_ex": (ctypes.c_int, [_vp] * 6),
         "gmm_apply_host": (ctypes.c_int, [_vp] * 4),

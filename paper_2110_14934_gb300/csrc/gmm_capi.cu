@@ -624,6 +624,14 @@ int gmm_state_set(gmm_t *h, int plane, int component, const float *src_host, siz
     return rc;
 }
 
+int gmm_inject_cuda_error(gmm_t *h, int cuda_error) {
+    if (!h || cuda_error == 0)
+        return fail(GMM_EINVAL, "gmm_inject_cuda_error: null handle or zero error code");
+    if (h->sticky == cudaSuccess)
+        h->sticky = static_cast<cudaError_t>(cuda_error);
+    return GMM_OK;
+}
+
 int gmm_reset(gmm_t *h) {
     if (!h)
         return fail(GMM_EINVAL, "gmm_reset: null handle");

@@ -446,6 +446,14 @@ int gmm_pool_submit_many(gmm_pool_t *p, int n, const int *cams, const uint8_t *c
     return GMM_OK;
 }
 
+int gmm_pool_inject_cuda_error(gmm_pool_t *p, int cuda_error) {
+    if (!p || cuda_error == 0)
+        return fail(GMM_EINVAL, "gmm_pool_inject_cuda_error: null pool or zero error code");
+    if (p->sticky == cudaSuccess)
+        p->sticky = static_cast<cudaError_t>(cuda_error);
+    return GMM_OK;
+}
+
 int gmm_pool_tick(gmm_pool_t *p) {
     if (!p)
         return fail(GMM_EINVAL, "gmm_pool_tick: null pool");

@@ -160,3 +160,38 @@ def test_bounded_wait_runs_out_and_reports():
         g.apply(r_, d_)
     torch.cuda.synchronize()
     g.sync()
+
+
+def test_sticky_cuda_error_through_the_test_hook():
+    """A CUDA failure recorded on a handle (injected on the host, no GPU
+    fault) makes every later launching or copying call fail with GMM_ECUDA
+    and a message naming the error; destroying the handle still works. The
+    same for a pool."""
+    import torch
+    H, W = 24, 40
+    rgb, depth, _ = scene_frames(4, H, W, 0, 0, 2)
+    g = G.GMM(H, W, 3)
+    r, d = to_dev(rgb[0], depth[0])
+    g.apply(r, d)
+    torch.cuda.synchronize()
+    L = G.load_library()
+    assert L.gmm_inject_cuda_error(g._h, 999) == G.OK  # cudaErrorUnknown
+    with pytest.raises(G.GMMError) as ei:
+        g.apply(r, d)
+    assert ei.value.code == G.ECUDA and "earlier CUDA failure" in str(ei.value)
+    with pytest.raises(G.GMMError) as ei:
+        g.sync()
+    assert ei.value.code == G.ECUDA
+    g.close()
+    assert L.gmm_inject_cuda_error(None, 999) == G.EINVAL
+    pool = G.Pool(max_cams=2)
+    cam = pool.admit(H, W, 3)
+    m = torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda")
+    pool.submit(cam, r, d, m)
+    pool.tick()
+    assert L.gmm_pool_inject_cuda_error(pool._p, 999) == G.OK
+    pool.submit(cam, r, d, m)
+    with pytest.raises(G.GMMError) as ei:
+        pool.tick()
+    assert ei.value.code == G.ECUDA
+    pool.close()

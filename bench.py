@@ -848,7 +848,16 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
     events = serving_schedule(len(cams), duration, wl["fps"], wl["session_frames"] / wl["fps"],
                               wl["live_fraction"], seed)
     n_slot = queue_depth + 4
-    masks = {}
+    # every camera's mask buffers, carved from one page-locked allocation made
+    # before the clock starts (allocating page-locked memory in the loop
+    # stalls the client)
+    words = [H * G.mask_words_per_row(W) for (H, W, _, _) in cams]
+    pinned = torch.empty(sum(words) * n_slot, dtype=torch.int32).pin_memory()
+    masks, off = {}, 0
+    for c, (H, W, _, _) in enumerate(cams):
+        for slot in range(n_slot):
+            masks[(c, slot)] = pinned[off:off + words[c]].view(H, G.mask_words_per_row(W))
+            off += words[c]
     live = {}          # camera -> server id of its current session
     slot_ticket = {}   # (camera, slot) -> ticket using that mask buffer
     rel_q = pyqueue.Queue()
@@ -867,7 +876,9 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
     import threading as th
     rt = th.Thread(target=releaser, daemon=True)
     rt.start()
-    tickets, lag = [], []
+    tickets, lag, admit_ms = [], [], []
+    import gc
+    gc.disable()  # no collector pauses in the client's real-time loop
     t0 = srv.now() + 0.5
     for (t, kind, c, k) in events:
         due = t0 + t
@@ -878,11 +889,13 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
             time.sleep(d - 0.0005) if d > 0.001 else None
         H, W, M, _ = cams[c]
         if kind == 0:
+            ta = time.perf_counter()
             try:
                 live[c] = srv.admit(H, W, M, **PARAMS)
             except G.GMMError as e:
                 if e.code != G.EBUDGET:
                     raise
+            admit_ms.append((time.perf_counter() - ta) * 1e3)
         elif kind == 2:
             sid = live.pop(c, None)
             if sid is not None:
@@ -894,9 +907,6 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
             old = slot_ticket.get((c, slot))
             if old is not None and not srv.done(old):
                 srv.wait(old, 60000)
-            if (c, slot) not in masks:
-                masks[(c, slot)] = torch.empty((H, G.mask_words_per_row(W)),
-                                               dtype=torch.int32).pin_memory()
             f = (k + c) % rgb_h.shape[0]
             lag.append((srv.now() - due) * 1e3)
             try:
@@ -909,6 +919,7 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
     for tk in tickets:
         srv.wait(tk, 60000)
     t_end = srv.now()
+    gc.enable()
     for sid in list(live.values()):
         rel_q.put(sid)
     rel_q.put(None)
@@ -917,7 +928,8 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
     lat = np.sort(srv.latencies_ms())
     srv.close()
     lag.sort()
-    return st, lat, t_end - t0, lag, rel_err
+    admit_ms.sort()
+    return st, lat, t_end - t0, lag, rel_err, admit_ms
 
 
 def run_serving(args, wl):
@@ -941,13 +953,13 @@ def run_serving(args, wl):
         ring.append((r.cpu().pin_memory(), d.cpu().pin_memory()))
     duration = args.serve_seconds or wl["duration_s"]
     barrier(world, dev)
-    st, lat, wall, lag, rel_err = serve_run(G, torch, cams, ring, wl,
+    st, lat, wall, lag, rel_err, admit_ms = serve_run(G, torch, cams, ring, wl,
                                             int(wl["budget_gb"] * 1e9), duration, 2021 + rank)
     wall = reduce_max(wall, world, dev)
     pixels = st["pixels"]
     total_px = pixels * world  # weak scaling: every rank serves its own cameras
     value = total_px / wall / 1e6
-    st2, lat2, _, _, _ = serve_run(G, torch, cams, ring, wl, int(wl["tight_budget_gb"] * 1e9),
+    st2, lat2, _, _, _, _ = serve_run(G, torch, cams, ring, wl, int(wl["tight_budget_gb"] * 1e9),
                                    wl["tight_duration_s"], 77 + rank)
     mean_bpp = sum(H * W * bytes_per_pixel(M, wl["prec"]) for (H, W, M, _) in cams) / \
         sum(H * W for (H, W, _, _) in cams)
@@ -972,6 +984,8 @@ def run_serving(args, wl):
                         "sessions_admitted": st["admitted"], "admissions_rejected": st["rejected"],
                         "ticks": st["ticks"], "mean_frames_per_tick": st["completed"] / max(st["ticks"], 1),
                         "driver_lag_ms_p99": fnum(pct(lag, 99)), "release_errors": len(rel_err),
+                        "admit_ms_p50": fnum(pct(admit_ms, 50)), "admit_ms_max":
+                            fnum(admit_ms[-1]) if admit_ms else None,
                         "budget_gb": wl["budget_gb"]},
             "tight_budget": {"budget_gb": wl["tight_budget_gb"], "duration_s": wl["tight_duration_s"],
                              "sessions_admitted": st2["admitted"], "admissions_rejected": st2["rejected"],

@@ -318,6 +318,18 @@ int state_set_common(const gmm_config &c, const Layout &L, void *arena, cudaStre
     return GMM_OK;
 }
 
+cudaError_t make_retaining_pool(int device, uint64_t keep_bytes, cudaMemPool_t *out) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaError_t e = cudaMemPoolCreate(out, &props);
+    if (e == cudaSuccess)
+        e = cudaMemPoolSetAttribute(*out, cudaMemPoolAttrReleaseThreshold, &keep_bytes);
+    return e;
+}
+
 int wait_event(cudaEvent_t ev, int timeout_ms, cudaError_t *sticky, const char *what) {
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {

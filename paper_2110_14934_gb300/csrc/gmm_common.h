@@ -46,4 +46,9 @@ int state_set_common(const gmm_config &c, const Layout &L, void *arena, cudaStre
                      cudaError_t *sticky, int plane, int comp, const float *src, size_t n);
 int wait_event(cudaEvent_t ev, int timeout_ms, cudaError_t *sticky, const char *what);
 
+// A stream-ordered memory pool on `device` that keeps up to `keep_bytes` of
+// freed memory mapped (the default pool returns it to the system at the next
+// synchronisation, so cameras that join later would pay for mapping again).
+cudaError_t make_retaining_pool(int device, uint64_t keep_bytes, cudaMemPool_t *out);
+
 } // namespace gmmlib

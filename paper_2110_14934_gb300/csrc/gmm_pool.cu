@@ -75,6 +75,7 @@ struct gmm_pool {
     std::vector<PoolCam> cams;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr; // graph capture (the legacy stream cannot capture)
+    cudaMemPool_t mempool = nullptr;   // cameras' state; keeps freed memory mapped
     cudaError_t sticky = cudaSuccess;
     int threads = 128, ctas_per_sm = 0, tile_pixels = 2048;
     CamView *d_views = nullptr;
@@ -340,6 +341,9 @@ gmm_pool_t *gmm_pool_create(size_t budget_bytes, int precision, int max_cams) {
         e = cudaMalloc(&p->d_counter, sizeof(int));
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = make_retaining_pool(p->device, budget_bytes ? (uint64_t)budget_bytes : UINT64_MAX,
+                                &p->mempool);
     for (int b = 0; b < kStaging && e == cudaSuccess; ++b) {
         e = cudaMallocHost(&p->h_views[b], sizeof(CamView) * (size_t)max_cams);
         if (e == cudaSuccess)
@@ -380,7 +384,7 @@ int gmm_pool_admit(gmm_pool_t *p, const gmm_config *cfg) {
         return fail(GMM_ENOMEM, "gmm_pool_admit: every slot is taken");
     DeviceGuard g(p->device);
     void *arena = nullptr;
-    cudaError_t e = cudaMallocAsync(&arena, L.total, p->stream);
+    cudaError_t e = cudaMallocFromPoolAsync(&arena, L.total, p->mempool, p->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(arena, 0, L.total, p->stream);
     if (e != cudaSuccess) {
@@ -697,6 +701,8 @@ int gmm_pool_destroy(gmm_pool_t *p) {
         if (c.used && c.arena)
             cudaFreeAsync(c.arena, p->stream);
     cudaStreamSynchronize(p->stream);
+    if (p->mempool)
+        cudaMemPoolDestroy(p->mempool);
     if (p->d_views)
         cudaFree(p->d_views);
     if (p->d_tile_begin)

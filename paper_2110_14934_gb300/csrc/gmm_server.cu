@@ -64,6 +64,7 @@ struct gmm_server {
     std::vector<SrvCam> cams;
     cudaStream_t s_up = nullptr, s_comp = nullptr, s_down = nullptr;
     cudaEvent_t ev_up = nullptr, ev_comp = nullptr, ev_alloc = nullptr;
+    cudaMemPool_t mempool = nullptr; // staging buffers; keeps freed memory mapped
     std::mutex mu;      // queues, tickets, counters, slots
     std::mutex pool_mu; // every call into the pool and stream-ordered allocation
     std::condition_variable cv_work, cv_done;
@@ -257,6 +258,9 @@ gmm_server_t *gmm_server_create(size_t budget_bytes, int precision, int max_cams
         e = cudaEventCreateWithFlags(&s->ev_comp, cudaEventDisableTiming);
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&s->ev_alloc, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = make_retaining_pool(s->device, budget_bytes ? (uint64_t)budget_bytes : UINT64_MAX,
+                                &s->mempool);
     if (e != cudaSuccess) {
         cuda_fail(nullptr, e, "gmm_server_create");
         gmm_server_destroy(s, 0);
@@ -312,7 +316,7 @@ int gmm_server_admit(gmm_server_t *s, const gmm_config *cfg) {
         pid = gmm_pool_admit(s->pool, cfg);
         cudaError_t e = cudaSuccess;
         if (pid >= 0) {
-            e = cudaMallocAsync(&buf, staging, s->s_comp);
+            e = cudaMallocFromPoolAsync(&buf, staging, s->mempool, s->s_comp);
             if (e == cudaSuccess)
                 e = cudaEventRecord(s->ev_alloc, s->s_comp);
             if (e == cudaSuccess) // uploads may only start once the buffer exists
@@ -474,11 +478,13 @@ int gmm_server_destroy(gmm_server_t *s, int timeout_ms) {
         s->engine.join();
     }
     DeviceGuard g(s->device);
-    if (s->s_comp)
-        cudaStreamSynchronize(s->s_comp);
     for (auto &c : s->cams)
         if (c.d_buf)
-            cudaFree(c.d_buf);
+            cudaFreeAsync(c.d_buf, s->s_comp); // after any queued use on the stream
+    if (s->s_comp)
+        cudaStreamSynchronize(s->s_comp);
+    if (s->mempool)
+        cudaMemPoolDestroy(s->mempool);
     if (s->pool)
         gmm_pool_destroy(s->pool);
     for (cudaEvent_t ev : s->ev_pool)

@@ -394,8 +394,10 @@ int gmm_pool_autotune_online(gmm_pool_t *p, int ticks_per_shape);
  * the non-NULL outputs. */
 int gmm_pool_tuning(gmm_pool_t *p, int *threads, int *ctas_per_sm, int *tile_pixels);
 
-/* Capture the pool's tick in a CUDA graph (enable = 1) and replay it while
- * the set of submitted cameras and their buffers is unchanged. */
+/* Run the pool's tick as a CUDA graph (enable = 1): the graph of the tick's
+ * launches is built once and replayed every tick, its kernel nodes updated
+ * with the tick's cameras; it is rebuilt when the number of launches (one
+ * per 128 cameras), the launch shape or the kernel instance changes. */
 int gmm_pool_use_graph(gmm_pool_t *p, int enable);
 
 /* As gmm_state_get, for camera cam. */

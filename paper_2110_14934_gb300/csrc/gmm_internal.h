@@ -54,17 +54,36 @@ cudaError_t launch_morph_open3(const uint32_t *in, uint32_t *out, int H, int W,
 
 // Multi-camera persistent tick. The worklist is implicit: job j covers tiles
 // [tile_begin[j], tile_begin[j+1]) of camera views[j], tile_pixels pixels
-// each (the last one of a camera ragged). counter must be zero at launch.
+// each (the last one of a camera ragged). A launch handles up to kPoolViews
+// cameras (a tick with more is split into several launches); its PoolArgs
+// are copied into the kernel's constant memory on the stream right before
+// it. *counter must be zero at launch; the launch zeroes the n_reset
+// counters at reset (the next tick's).
+constexpr int kPoolViews = 128;
 struct PoolArgs {
-    const gmmdev::CamView *views;
-    const int64_t *tile_begin; // n_jobs + 1 entries
+    gmmdev::CamView views[kPoolViews];
+    int64_t tile_begin[kPoolViews + 1];
     int *counter;
+    int *reset;
+    int n_reset;
     int n_jobs;
     int tile_pixels;
     int64_t n_tiles;
 };
-cudaError_t launch_pool_tick_impl(const PoolArgs &a, int threads, int blocks, int prec,
+static_assert(sizeof(PoolArgs) <= 32768, "one launch's arguments fit half the constant bank");
+
+// Upload *args_host (page-locked for an asynchronous copy) to the kernel's
+// constant memory and launch the pool kernel; all_variants: the instance
+// that also handles the options and the augmentation alternative.
+cudaError_t launch_pool_tick_impl(const PoolArgs *args_host, int threads, int blocks, int prec,
                                   bool all_variants, cudaStream_t s);
+
+// The constant-memory argument bank is shared by every pool on a device:
+// enqueue uploads and launches between acquire (takes the device's lock and
+// orders stream s after the bank's previous user) and release (records s as
+// the last user, drops the lock). Not needed while capturing a graph.
+cudaError_t pool_bank_acquire(int device, cudaStream_t s);
+cudaError_t pool_bank_release(int device, cudaStream_t s);
 
 // process_pixel variant a camera needs: 0 default, 1 learning-rate/variance
 // options, 2 augmentation alternative.

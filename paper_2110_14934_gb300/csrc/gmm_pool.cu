@@ -30,18 +30,18 @@ struct PoolCam {
     uint32_t *mask = nullptr, *fgr = nullptr, *fgd = nullptr;
 };
 
+// What a captured graph depends on. The views and tile tables are read at
+// replay from the page-locked staging buffer the graph was captured with.
 struct GraphSig {
-    int n_jobs = -1, threads = 0, blocks = 0, tile_pixels = 0;
-    int64_t n_tiles = -1;
+    int n_launch = -1, threads = 0, blocks = 0;
     bool all_variants = false;
     bool operator==(const GraphSig &o) const {
-        return n_jobs == o.n_jobs && threads == o.threads && blocks == o.blocks &&
-               tile_pixels == o.tile_pixels && n_tiles == o.n_tiles &&
+        return n_launch == o.n_launch && threads == o.threads && blocks == o.blocks &&
                all_variants == o.all_variants;
     }
 };
 
-constexpr int kStaging = 2;
+constexpr int kStaging = 2; // page-locked argument buffers, used alternately
 
 struct Shape {
     int threads, ctas, tile;
@@ -78,11 +78,12 @@ struct gmm_pool {
     cudaMemPool_t mempool = nullptr;   // cameras' state; keeps freed memory mapped
     cudaError_t sticky = cudaSuccess;
     int threads = 128, ctas_per_sm = 0, tile_pixels = 2048;
-    CamView *d_views = nullptr;
-    int64_t *d_tile_begin = nullptr;
-    int *d_counter = nullptr;
-    CamView *h_views[kStaging] = {};
-    int64_t *h_tile_begin[kStaging] = {};
+    // Tile counters, two sets of kmax (one per launch of a tick): a tick
+    // uses set `parity` and its launches zero the other set for the next.
+    int *d_counters = nullptr;
+    int kmax = 1, parity = 0;
+    // Launch arguments (kmax per tick) in page-locked memory, two buffers.
+    gmmhost::PoolArgs *h_args[kStaging] = {};
     cudaEvent_t ev_staged[kStaging] = {};
     bool staged_used[kStaging] = {};
     int buf = 0;
@@ -109,28 +110,6 @@ static int blocks_for(const gmm_pool *p) {
     if (per_sm < 1)
         per_sm = 1;
     return gmmhost::num_sms() * per_sm;
-}
-
-// Enqueue the tick's table uploads, counter reset and the persistent launch.
-static cudaError_t enqueue_body(gmm_pool *p, cudaStream_t s, int b, int n_jobs, int64_t n_tiles,
-                                int blocks, bool all_variants) {
-    cudaError_t e = cudaMemcpyAsync(p->d_views, p->h_views[b], sizeof(CamView) * n_jobs,
-                                    cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(p->d_tile_begin, p->h_tile_begin[b], sizeof(int64_t) * (n_jobs + 1),
-                            cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), s);
-    if (e != cudaSuccess)
-        return e;
-    gmmhost::PoolArgs a;
-    a.views = p->d_views;
-    a.tile_begin = p->d_tile_begin;
-    a.counter = p->d_counter;
-    a.n_jobs = n_jobs;
-    a.tile_pixels = p->tile_pixels;
-    a.n_tiles = n_tiles;
-    return gmmhost::launch_pool_tick_impl(a, p->threads, blocks, p->prec, all_variants, s);
 }
 
 // Candidate launch shapes: block sizes, full or half residency, tile sizes.
@@ -199,6 +178,67 @@ static int tuning_poll(gmm_pool *p, bool block) {
     return GMM_OK;
 }
 
+// Enqueue the tick's launches (argument upload + persistent kernel each)
+// from staging buffer b.
+static cudaError_t enqueue_body(gmm_pool *p, cudaStream_t s, int b, int n_launch, int blocks,
+                                bool all_variants) {
+    cudaError_t e = cudaSuccess;
+    for (int li = 0; li < n_launch && e == cudaSuccess; ++li)
+        e = gmmhost::launch_pool_tick_impl(&p->h_args[b][li], p->threads, blocks, p->prec,
+                                           all_variants, s);
+    return e;
+}
+
+// Launch the tick, directly or by replaying the graph captured for staging
+// buffer b (captured again when its shape changed).
+static cudaError_t launch_tick(gmm_pool *p, int b, int n_launch, bool all_variants) {
+    const int blocks = blocks_for(p);
+    if (!p->use_graph) {
+        cudaError_t e = gmmhost::pool_bank_acquire(p->device, p->stream);
+        if (e != cudaSuccess)
+            return e;
+        e = enqueue_body(p, p->stream, b, n_launch, blocks, all_variants);
+        const cudaError_t er = gmmhost::pool_bank_release(p->device, p->stream);
+        return e != cudaSuccess ? e : er;
+    }
+    GraphSig sig;
+    sig.n_launch = n_launch;
+    sig.threads = p->threads;
+    sig.blocks = blocks;
+    sig.all_variants = all_variants;
+    cudaError_t e = cudaSuccess;
+    if (!(p->gexec[b] && p->gsig[b] == sig)) {
+        if (p->gexec[b])
+            cudaGraphExecDestroy(p->gexec[b]);
+        p->gexec[b] = nullptr;
+        p->gsig[b] = GraphSig();
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t eb = enqueue_body(p, p->cap_stream, b, n_launch, blocks,
+                                                all_variants);
+            e = cudaStreamEndCapture(p->cap_stream, &g);
+            if (eb != cudaSuccess)
+                e = eb;
+        }
+        if (e == cudaSuccess)
+            e = cudaGraphInstantiate(&p->gexec[b], g, 0);
+        if (g)
+            cudaGraphDestroy(g);
+        if (e == cudaSuccess)
+            p->gsig[b] = sig;
+    }
+    if (e == cudaSuccess)
+        e = gmmhost::pool_bank_acquire(p->device, p->stream);
+    if (e == cudaSuccess) {
+        e = cudaGraphLaunch(p->gexec[b], p->stream);
+        const cudaError_t er = gmmhost::pool_bank_release(p->device, p->stream);
+        if (e == cudaSuccess)
+            e = er;
+    }
+    return e;
+}
+
 // One tick over the submitted cameras. clear: drop the submissions and mark
 // the cameras initialised afterwards (false while autotuning).
 static int pool_tick_impl(gmm_pool *p, bool clear) {
@@ -207,15 +247,8 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         n_jobs += (c.used && c.submitted) ? 1 : 0;
     if (n_jobs == 0)
         return GMM_OK;
-    const int b = p->buf;
-    if (p->staged_used[b]) {
-        // The upload that last read this staging buffer must have run.
-        const int rc = wait_event(p->ev_staged[b], 60000, &p->sticky, "gmm_pool_tick staging");
-        if (rc != GMM_OK)
-            return rc;
-    }
-    // An online-tuning trial sets its launch shape first: the tile table
-    // below depends on the tile size.
+    // An online-tuning trial sets its launch shape first: the tile tables
+    // below depend on the tile size.
     Tuning &tu = p->tune;
     const bool trial = clear && tu.active && tu.issued < (int)tu.cands.size() * tu.per_shape;
     Trial tr{};
@@ -226,20 +259,47 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         p->ctas_per_sm = tu.cands[tr.cand].ctas;
         p->tile_pixels = tu.cands[tr.cand].tile;
     }
-    int j = 0;
+    const int b = p->buf;
+    if (p->staged_used[b]) {
+        // The uploads that last read this staging buffer must have run.
+        const int rc = wait_event(p->ev_staged[b], 60000, &p->sticky, "gmm_pool_tick staging");
+        if (rc != GMM_OK)
+            return rc;
+    }
+    // The launches' arguments: up to kPoolViews cameras each.
+    int *cur = p->d_counters + p->parity * p->kmax;
+    int *next = p->d_counters + (1 - p->parity) * p->kmax;
+    int li = 0, j = 0;
     int64_t tiles = 0;
     bool all_variants = false; // some camera needs the options or the augmented mixture
+    auto close_launch = [&]() {
+        gmmhost::PoolArgs &a = p->h_args[b][li];
+        a.tile_begin[j] = tiles;
+        a.n_jobs = j;
+        a.n_tiles = tiles;
+        a.tile_pixels = p->tile_pixels;
+        a.counter = cur + li;
+        a.reset = next;
+        a.n_reset = p->kmax;
+        ++li;
+        j = 0;
+        tiles = 0;
+    };
     for (PoolCam &c : p->cams) {
         if (!(c.used && c.submitted))
             continue;
-        p->h_views[b][j] = make_view(c.cfg, c.L, c.arena, c.rgb, c.depth, c.mask, c.fgr, c.fgd,
-                                     c.initialized ? 0 : 1);
-        all_variants = all_variants || gmmhost::view_variant(p->h_views[b][j]) != 0;
-        p->h_tile_begin[b][j] = tiles;
+        gmmhost::PoolArgs &a = p->h_args[b][li];
+        a.views[j] = make_view(c.cfg, c.L, c.arena, c.rgb, c.depth, c.mask, c.fgr, c.fgd,
+                               c.initialized ? 0 : 1);
+        all_variants = all_variants || gmmhost::view_variant(a.views[j]) != 0;
+        a.tile_begin[j] = tiles;
         tiles += (c.L.n_pad + p->tile_pixels - 1) / p->tile_pixels;
-        ++j;
+        if (++j == gmmhost::kPoolViews)
+            close_launch();
     }
-    p->h_tile_begin[b][n_jobs] = tiles;
+    if (j > 0)
+        close_launch();
+    const int n_launch = li;
     cudaError_t e = cudaSuccess;
     if (trial) {
         e = cudaEventCreate(&tr.a);
@@ -250,40 +310,7 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         if (e != cudaSuccess)
             return cuda_fail(&p->sticky, e, "gmm_pool_tick tuning");
     }
-    const int blocks = blocks_for(p);
-    if (p->use_graph) {
-        GraphSig sig;
-        sig.n_jobs = n_jobs;
-        sig.threads = p->threads;
-        sig.blocks = blocks;
-        sig.tile_pixels = p->tile_pixels;
-        sig.n_tiles = tiles;
-        sig.all_variants = all_variants;
-        if (!(p->gexec[b] && p->gsig[b] == sig)) {
-            if (p->gexec[b])
-                cudaGraphExecDestroy(p->gexec[b]);
-            p->gexec[b] = nullptr;
-            cudaGraph_t g = nullptr;
-            e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                const cudaError_t eb = enqueue_body(p, p->cap_stream, b, n_jobs, tiles, blocks,
-                                                     all_variants);
-                e = cudaStreamEndCapture(p->cap_stream, &g);
-                if (eb != cudaSuccess)
-                    e = eb;
-            }
-            if (e == cudaSuccess)
-                e = cudaGraphInstantiate(&p->gexec[b], g, 0);
-            if (g)
-                cudaGraphDestroy(g);
-            if (e == cudaSuccess)
-                p->gsig[b] = sig;
-        }
-        if (e == cudaSuccess)
-            e = cudaGraphLaunch(p->gexec[b], p->stream);
-    } else {
-        e = enqueue_body(p, p->stream, b, n_jobs, tiles, blocks, all_variants);
-    }
+    e = launch_tick(p, b, n_launch, all_variants);
     if (e == cudaSuccess && trial) {
         e = cudaEventRecord(tr.b, p->stream);
         if (e == cudaSuccess) {
@@ -297,6 +324,7 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         return cuda_fail(&p->sticky, e, "gmm_pool_tick");
     p->staged_used[b] = true;
     p->buf = (b + 1) % kStaging;
+    p->parity ^= 1;
     if (clear) {
         for (PoolCam &c : p->cams) {
             if (c.used && c.submitted) {
@@ -332,25 +360,22 @@ gmm_pool_t *gmm_pool_create(size_t budget_bytes, int precision, int max_cams) {
     p->prec = precision;
     p->max_cams = max_cams;
     p->cams.resize((size_t)max_cams);
+    p->kmax = (max_cams + gmmhost::kPoolViews - 1) / gmmhost::kPoolViews;
     cudaError_t e = cudaGetDevice(&p->device);
-    if (e == cudaSuccess)
-        e = cudaMalloc(&p->d_views, sizeof(CamView) * (size_t)max_cams);
-    if (e == cudaSuccess)
-        e = cudaMalloc(&p->d_tile_begin, sizeof(int64_t) * ((size_t)max_cams + 1));
-    if (e == cudaSuccess)
-        e = cudaMalloc(&p->d_counter, sizeof(int));
-    if (e == cudaSuccess)
-        e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess)
-        e = make_retaining_pool(p->device, budget_bytes ? (uint64_t)budget_bytes : UINT64_MAX,
-                                &p->mempool);
     for (int b = 0; b < kStaging && e == cudaSuccess; ++b) {
-        e = cudaMallocHost(&p->h_views[b], sizeof(CamView) * (size_t)max_cams);
-        if (e == cudaSuccess)
-            e = cudaMallocHost(&p->h_tile_begin[b], sizeof(int64_t) * ((size_t)max_cams + 1));
+        e = cudaMallocHost(&p->h_args[b], sizeof(gmmhost::PoolArgs) * (size_t)p->kmax);
         if (e == cudaSuccess)
             e = cudaEventCreateWithFlags(&p->ev_staged[b], cudaEventDisableTiming);
     }
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&p->d_counters, sizeof(int) * 2 * (size_t)p->kmax);
+    if (e == cudaSuccess)
+        e = cudaMemset(p->d_counters, 0, sizeof(int) * 2 * (size_t)p->kmax);
+    if (e == cudaSuccess)
+        e = make_retaining_pool(p->device, budget_bytes ? (uint64_t)budget_bytes : UINT64_MAX,
+                                &p->mempool);
     if (e != cudaSuccess) {
         fail(e == cudaErrorMemoryAllocation ? GMM_ENOMEM : GMM_ECUDA,
              std::string("gmm_pool_create: ") + cudaGetErrorString(e));
@@ -703,19 +728,13 @@ int gmm_pool_destroy(gmm_pool_t *p) {
     cudaStreamSynchronize(p->stream);
     if (p->mempool)
         cudaMemPoolDestroy(p->mempool);
-    if (p->d_views)
-        cudaFree(p->d_views);
-    if (p->d_tile_begin)
-        cudaFree(p->d_tile_begin);
-    if (p->d_counter)
-        cudaFree(p->d_counter);
+    if (p->d_counters)
+        cudaFree(p->d_counters);
     if (p->cap_stream)
         cudaStreamDestroy(p->cap_stream);
     for (int b = 0; b < kStaging; ++b) {
-        if (p->h_views[b])
-            cudaFreeHost(p->h_views[b]);
-        if (p->h_tile_begin[b])
-            cudaFreeHost(p->h_tile_begin[b]);
+        if (p->h_args[b])
+            cudaFreeHost(p->h_args[b]);
         if (p->ev_staged[b])
             cudaEventDestroy(p->ev_staged[b]);
     }

@@ -186,3 +186,88 @@ def test_pool_online_tuning_changes_nothing_but_speed():
     assert not tuning
     assert shape["threads"] in (64, 128, 256) and shape["tile_pixels"] % shape["threads"] == 0
     pool.sync()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_pool_more_cameras_than_one_launch_holds(graph):
+    """A tick with more cameras than one launch's parameter block holds (128)
+    is split into several launches; every camera still equals its run alone,
+    in ticks of changing size (the graph's nodes updated or rebuilt)."""
+    import torch
+    n_cams, n = 131, 4
+    shapes = [(8 + (i % 3), 33 + 7 * (i % 5), 3 + (i % 3)) for i in range(n_cams)]
+    frames = [scene_frames(3000 + i, H, W, i % 2, 0, n) for i, (H, W, M) in enumerate(shapes)]
+    schedule = [set(range(n_cams)), set(range(n_cams)), set(range(0, n_cams, 2)),
+                set(range(n_cams))]
+    alone = {}
+    for i, (H, W, M) in enumerate(shapes):
+        g = G.GMM(H, W, M)
+        k = 0
+        for t, active in enumerate(schedule):
+            if i in active:
+                r, d = to_dev(frames[i][0][k], frames[i][1][k])
+                alone[(i, t)] = words(g.apply(r, d)).copy()
+                k += 1
+        torch.cuda.synchronize()
+        alone[i] = g.planes()
+        g.close()
+    pool = G.Pool(max_cams=n_cams)
+    pool.use_graph(graph)
+    ids = [pool.admit(H, W, M) for (H, W, M) in shapes]
+    pos = [0] * n_cams
+    got = {}
+    for t, active in enumerate(schedule):
+        masks = {}
+        for i in sorted(active):
+            H, W, M = shapes[i]
+            r, d = to_dev(frames[i][0][pos[i]], frames[i][1][pos[i]])
+            m = torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda")
+            masks[i] = (m, r, d)
+            pool.submit(ids[i], r, d, m)
+            pos[i] += 1
+        pool.tick()
+        torch.cuda.synchronize()
+        for i in active:
+            got[(i, t)] = words(masks[i][0]).copy()
+    for i in range(n_cams):
+        got[i] = pool.planes(ids[i])
+    pool.close()
+    assert alone.keys() == got.keys()
+    for key in alone:
+        assert np.array_equal(alone[key], got[key]), key
+
+
+def test_two_pools_on_two_streams():
+    """Two pools ticking on two streams without synchronising in between
+    (their launches share the device's argument bank, taken in turn): each
+    camera still equals its run alone."""
+    import torch
+    n = 6
+    frames = _frames(n)
+    a = _alone(frames, [set(range(len(CAMS)))] * n)
+    halves = [list(range(0, len(CAMS), 2)), list(range(1, len(CAMS), 2))]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    pools = [G.Pool(max_cams=8), G.Pool(max_cams=8)]
+    pools[1].use_graph(True)
+    ids = [{i: pools[h].admit(*CAMS[i]) for i in halves[h]} for h in range(2)]
+    keep, masks = [], {}
+    torch.cuda.synchronize()
+    for t in range(n):
+        for h in range(2):
+            with torch.cuda.stream(streams[h]):
+                for i in halves[h]:
+                    H, W, M = CAMS[i]
+                    r = torch.from_numpy(np.ascontiguousarray(frames[i][0][t])).cuda()
+                    d = torch.from_numpy(np.ascontiguousarray(frames[i][1][t]).view(np.int16)).cuda()
+                    m = torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda")
+                    keep.append((r, d, m))
+                    masks[(i, t)] = m
+                    pools[h].submit(ids[h][i], r, d, m)
+                pools[h].tick(streams[h])
+    torch.cuda.synchronize()
+    for (i, t), m in masks.items():
+        assert np.array_equal(words(m), a[(i, t)]), (i, t)
+    for h in range(2):
+        for i in halves[h]:
+            assert np.array_equal(pools[h].planes(ids[h][i]), a[i]), i
+        pools[h].close()

@@ -63,7 +63,7 @@ FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129 * 1024 * 1024
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gmm_tick_f32_m5_1920x1080.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2110_14934_gb300", "csrc", f)
-                  for f in ("gmm_device.cuh", "gmm_kernels.cu", "gmm_staged.cu", "gmm_tma.cuh")]
+                  for f in ("gmm_device.cuh", "gmm_kernels.cu")]
 
 
 def bytes_per_pixel(M: int, prec: int) -> float:

@@ -11,8 +11,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libgmm.so")
-UNITS = ["gmm_kernels.cu", "gmm_staged.cu", "gmm_capi.cu", "gmm_pool.cu", "gmm_noalloc.cu",
-         "gmm_server.cu"]
+UNITS = ["gmm_kernels.cu", "gmm_pool_kernel.cu", "gmm_staged.cu", "gmm_capi.cu", "gmm_pool.cu",
+         "gmm_noalloc.cu", "gmm_server.cu"]
 ARCH = "103a"
 
 

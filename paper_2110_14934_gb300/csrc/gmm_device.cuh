@@ -90,7 +90,7 @@ __device__ __forceinline__ float var_sample(const StreamPrm &p, float d2) {
 }
 
 // Everything one tick of one camera needs; passed by value to the
-// single-camera kernel, read from a device table by the pooled kernel.
+// single-camera kernel, read from constant memory by the pooled kernel.
 struct CamView {
     void *planes;          // n_tiles tiles of M*8 planes of kTile elements
     uint8_t *fusion;       // n_tiles*kTile List-1 bytes, indexed by padded pixel

@@ -387,6 +387,12 @@ def run_reference(args, wl):
     return 0
 
 
+def model_flags(args, G) -> int:
+    """Model flags the options ask for (storage options only; the method's
+    readings stay the default)."""
+    return G.FLAG_STOCHASTIC_WEIGHTS if getattr(args, "stochastic_weights", False) else 0
+
+
 def config_dict(key, wl, world):
     state_mb = wl["H"] * wl["W"] * wl["M"] * (32 if wl["prec"] == 0 else 16) / 1e6
     return {"workload": f"{key}: {wl['name']}", "H": wl["H"], "W": wl["W"], "M": wl["M"],
@@ -416,7 +422,7 @@ def run_gmm(args, wl):
     rgb_d, dep_d, _ = synth.frames_device(scene, 0, nf, device=dev, with_gt=False)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
-    g = G.GMM(H, W, M, precision=prec, device=dev, **PARAMS)
+    g = G.GMM(H, W, M, precision=prec, device=dev, flags=model_flags(args, G), **PARAMS)
     g.set_kernel(KERNELS[args.kernel], args.variant, args.ctas)
     mask = g.new_mask()
     K, Wm = args.steps, args.warmup
@@ -542,6 +548,8 @@ def run_gmm(args, wl):
         if morph_info:
             line["config"]["morph_open"] = True
             line["morph"] = morph_info
+        if model_flags(args, G):
+            line["config"]["weights_rounding"] = "stochastic"
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -605,7 +613,7 @@ def run_pool(args, wl):
     mask_ptr = [m.data_ptr() for m in masks]
 
     pool = G.Pool(precision=prec, max_cams=len(cams), device=dev)
-    ids = [pool.admit(H, W, M, **PARAMS) for (H, W, M, _) in cams]
+    ids = [pool.admit(H, W, M, flags=model_flags(args, G), **PARAMS) for (H, W, M, _) in cams]
     pool.set_stream(stream)
     graph = not args.no_graph
     pool.use_graph(graph)
@@ -728,6 +736,8 @@ def run_pool(args, wl):
             "gpu_launches": K,
             "clocks": clk,
         }
+        if model_flags(args, G):
+            line["config"]["weights_rounding"] = "stochastic"
         print(json.dumps(line), flush=True)
     pool.close()
     if world > 1:
@@ -1090,6 +1100,8 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="pooled workloads: default launch")
     ap.add_argument("--frames", type=int, default=0,
                     help="resident frames to cycle through (0: the workload's sequence length)")
+    ap.add_argument("--stochastic-weights", action="store_true",
+                    help="FP16 state: store the weights with stochastic rounding")
     ap.add_argument("--morph", action="store_true",
                     help="single-camera workloads: each step adds the 3x3 opening of the mask")
     ap.add_argument("--cpu-frames", type=int, default=21, help="oracle baseline frames (0 = skip)")

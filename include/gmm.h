@@ -130,6 +130,14 @@ typedef struct gmm_config {
  * default: v tracks the summed squared distance and sigma^2 = v / D. */
 #define GMM_FLAG_RHO_ETA 1u
 #define GMM_FLAG_VAR_PER_CHANNEL 2u
+/* Storage option, GMM_PREC_F16 only (not part of the method): the bfloat16
+ * weights are stored with stochastic rounding (round up with probability
+ * equal to the dropped fraction; random bits from a counter-based hash of
+ * the model's tick count, the pixel and the component), so a weight's
+ * expected stored value equals its FP32 value instead of stalling when an
+ * update is below half a bfloat16 step. Not available to
+ * gmm_apply_open3_noalloc, which has no tick count. */
+#define GMM_FLAG_STOCHASTIC_WEIGHTS 4u
 
 /* Fill *cfg with the given model parameters and the defaults above. */
 void gmm_config_init(gmm_config *cfg, int H, int W, int M, float alpha,

@@ -19,7 +19,7 @@ from . import _build
 __all__ = ["GMM", "Pool", "GMMError", "fuse_masks", "morph_open3", "mask_words_per_row",
            "state_bytes", "unpack_mask", "pack_mask", "load_library", "PLANES",
            "PREC_F32", "PREC_F16", "make_config", "MODE_FUSION", "MODE_AUGMENTED",
-           "FLAG_RHO_ETA", "FLAG_VAR_PER_CHANNEL"]
+           "FLAG_RHO_ETA", "FLAG_VAR_PER_CHANNEL", "FLAG_STOCHASTIC_WEIGHTS"]
 
 OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT = 0, -1, -2, -3, -4, -5
 PLANE_W_C, PLANE_MU_R, PLANE_MU_G, PLANE_MU_B, PLANE_V_C, PLANE_W_D, PLANE_MU_D, PLANE_V_D, \
@@ -29,7 +29,7 @@ PREC_F32, PREC_F16 = 0, 1
 PIPE_DEPTH = 3
 KERNEL_STAGED, KERNEL_DIRECT = 0, 1
 MODE_FUSION, MODE_AUGMENTED = 0, 1
-FLAG_RHO_ETA, FLAG_VAR_PER_CHANNEL = 1, 2
+FLAG_RHO_ETA, FLAG_VAR_PER_CHANNEL, FLAG_STOCHASTIC_WEIGHTS = 1, 2, 4
 
 _ERRNAMES = {EINVAL: "GMM_EINVAL", ENOMEM: "GMM_ENOMEM", ECUDA: "GMM_ECUDA",
              EBUDGET: "GMM_EBUDGET", ETIMEOUT: "GMM_ETIMEOUT"}

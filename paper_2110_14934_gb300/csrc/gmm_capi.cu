@@ -92,8 +92,10 @@ std::string check_config(const gmm_config *c) {
         return "mode must be GMM_MODE_FUSION or GMM_MODE_AUGMENTED";
     if (!(c->depth_scale > 0.f) || !std::isfinite(c->depth_scale))
         return "depth_scale must be a finite value > 0";
-    if (c->flags & ~(GMM_FLAG_RHO_ETA | GMM_FLAG_VAR_PER_CHANNEL))
+    if (c->flags & ~(GMM_FLAG_RHO_ETA | GMM_FLAG_VAR_PER_CHANNEL | GMM_FLAG_STOCHASTIC_WEIGHTS))
         return "flags: unknown bits";
+    if ((c->flags & GMM_FLAG_STOCHASTIC_WEIGHTS) && c->precision != GMM_PREC_F16)
+        return "GMM_FLAG_STOCHASTIC_WEIGHTS needs GMM_PREC_F16 state";
     return "";
 }
 
@@ -112,7 +114,7 @@ gmmdev::StreamPrm stream_prm(const gmm_config &c, bool depth) {
 
 CamView make_view(const gmm_config &c, const Layout &L, void *arena, const uint8_t *rgb,
                   const uint16_t *depth, uint32_t *mask, uint32_t *fgr, uint32_t *fgd,
-                  int first) {
+                  int first, uint32_t tick) {
     CamView v;
     std::memset(&v, 0, sizeof(v));
     v.planes = arena;
@@ -142,7 +144,10 @@ CamView make_view(const gmm_config &c, const Layout &L, void *arena, const uint8
     v.pd = stream_prm(c, true);
     if (c.mode == GMM_MODE_AUGMENTED)
         v.flags |= gmmdev::kModeAugmented;
+    if (c.flags & GMM_FLAG_STOCHASTIC_WEIGHTS)
+        v.flags |= gmmdev::kStochasticWeights;
     v.depth_scale = c.depth_scale;
+    v.tick = tick;
     return v;
 }
 
@@ -375,15 +380,17 @@ struct gmm_ctx {
     // tick kernel selection and the staged kernel's wait-status word
     int kernel = GMM_KERNEL_DIRECT, variant = 0, ctas_per_sm = 0;
     int *d_status = nullptr;
+    uint32_t ticks = 0; // ticks taken (seeds stochastic rounding)
 };
 
 static int launch_apply(gmm_ctx *h, const uint8_t *rgb, const uint16_t *depth, uint32_t *mask,
                         uint32_t *fgr, uint32_t *fgd) {
     uint32_t *tick_mask = h->cfg.morph_open ? h->morph_tmp : mask;
     CamView v = make_view(h->cfg, h->L, h->arena, rgb, depth, tick_mask, fgr, fgd,
-                          h->initialized ? 0 : 1);
+                          h->initialized ? 0 : 1, h->ticks);
     cudaError_t e;
-    if (h->initialized && h->kernel == GMM_KERNEL_STAGED && h->cfg.mode == GMM_MODE_FUSION)
+    if (h->initialized && h->kernel == GMM_KERNEL_STAGED && h->cfg.mode == GMM_MODE_FUSION &&
+        !(h->cfg.flags & GMM_FLAG_STOCHASTIC_WEIGHTS))
         e = gmmhost::launch_tick_staged(v, h->variant, h->ctas_per_sm, h->d_status, h->stream);
     else
         e = gmmhost::launch_tick(
@@ -395,6 +402,7 @@ static int launch_apply(gmm_ctx *h, const uint8_t *rgb, const uint16_t *depth, u
     if (e != cudaSuccess)
         return cuda_fail(&h->sticky, e, "gmm_apply launch");
     h->initialized = 1;
+    h->ticks += 1;
     return GMM_OK;
 }
 

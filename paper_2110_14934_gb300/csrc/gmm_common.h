@@ -35,7 +35,7 @@ std::string check_config(const gmm_config *c);
 gmmdev::StreamPrm stream_prm(const gmm_config &c, bool depth);
 gmmdev::CamView make_view(const gmm_config &c, const Layout &L, void *arena,
                           const uint8_t *rgb, const uint16_t *depth, uint32_t *mask,
-                          uint32_t *fgr, uint32_t *fgd, int first);
+                          uint32_t *fgr, uint32_t *fgd, int first, uint32_t tick);
 bool device_accessible(const void *p);
 std::string check_frame_ptrs(const uint8_t *rgb, const uint16_t *depth, uint32_t *mask,
                              uint32_t *fgr, uint32_t *fgd);

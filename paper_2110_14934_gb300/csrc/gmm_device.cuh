@@ -35,6 +35,7 @@ enum { F_WC = 0, F_MUR, F_MUG, F_MUB, F_VC, F_WD, F_MUD, F_VD };
 constexpr uint32_t kDepthStarted = 16u;
 constexpr int kStageInputs = 1;   // CamView.flags: frame bytes staged with the state
 constexpr int kModeAugmented = 2; // CamView.flags: one 4-channel mixture (R, G, B, s*depth)
+constexpr int kStochasticWeights = 4; // CamView.flags: BF16 weights stored with stochastic rounding
 constexpr uint32_t kRhoEta = 1u;        // StreamPrm.flags: rho = alpha * eta(x | mu, sigma)
 constexpr uint32_t kVarPerChannel = 2u; // StreamPrm.flags: v is the per-channel variance
 
@@ -102,9 +103,10 @@ struct CamView {
     int64_t n_tiles;       // state tiles: ceil(n_pad / kTile)
     int64_t n_pad;         // H*w_pad (< 2^30)
     int H, W, w_pad, wpr;  // wpr = words per mask row = w_pad / 32
-    int M, prec, first, flags; // flags: kStageInputs (staged launcher), kModeAugmented
+    int M, prec, first, flags; // flags: kStageInputs, kModeAugmented, kStochasticWeights
     uint32_t wpr_mul, wpr_shift; // n / wpr == umulhi(n, wpr_mul) >> wpr_shift (wpr > 1)
-    float depth_scale, pad2;     // augmented mode: depth (mm) to the colour byte range
+    float depth_scale;           // augmented mode: depth (mm) to the colour byte range
+    uint32_t tick;               // ticks the model has taken (seeds stochastic rounding)
     StreamPrm pc, pd;
 };
 
@@ -137,6 +139,28 @@ __device__ __forceinline__ uint32_t f16x2_pack_sat(float lo, float hi) {
     uint32_t r;
     asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
     return r;
+}
+
+// Stochastic rounding of non-negative floats to bfloat16 (the weights):
+// adding 16 uniform random bits below the kept ones and truncating rounds up
+// with probability equal to the dropped fraction, so the stored weight is
+// unbiased. The bits come from a counter-based hash of (tick, pixel, value):
+// MurmurHash3's 32-bit finaliser (Appleby), applied twice.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ uint32_t sr_bits(uint32_t tick, uint32_t p, uint32_t k) {
+    return fmix32(fmix32(tick * 0x9e3779b9u + p) ^ (k * 0x27d4eb2fu));
+}
+__device__ __forceinline__ uint32_t bf16x2_pack_sr(float lo, float hi, uint32_t r) {
+    const uint32_t l = (__float_as_uint(lo) + (r & 0xffffu)) >> 16;
+    const uint32_t h = (__float_as_uint(hi) + (r >> 16)) & 0xffff0000u;
+    return h | l;
 }
 
 // The eight values of one component at one pixel.
@@ -174,10 +198,11 @@ __device__ __forceinline__ Fields load_fields(const void *pl, int64_t e0, int64_
 }
 
 // kDepth: also write w_d and v_d (FP32 stores them separately; FP16 always
-// writes them with their group).
-template <int PREC, int M, bool kDepth = true>
+// writes them with their group). sr: nonzero = 32 random bits for the
+// stochastic rounding of the two weights (FP16/BF16 state, kSR builds only).
+template <int PREC, int M, bool kDepth = true, bool kSR = false>
 __device__ __forceinline__ void store_fields(void *pl, int64_t e0, int64_t tb, uint32_t t, int i,
-                                             const Fields &f) {
+                                             const Fields &f, uint32_t sr = 0u) {
     if constexpr (PREC == 0) {
         float *b = static_cast<float *>(pl) + e0 + kFields * i * kTile;
         b[F_WC * kTile] = f.wc;
@@ -192,7 +217,8 @@ __device__ __forceinline__ void store_fields(void *pl, int64_t e0, int64_t tb, u
             b[F_VD * kTile] = f.vd;
     } else {
         uint2 *g = static_cast<uint2 *>(pl) + (tb >> 2) + t + 2 * i * kTile;
-        g[0] = make_uint2(bf16x2_pack(f.wc, f.wd), f16x2_pack_sat(f.mur, f.mug));
+        const uint32_t w = (kSR && sr) ? bf16x2_pack_sr(f.wc, f.wd, sr) : bf16x2_pack(f.wc, f.wd);
+        g[0] = make_uint2(w, f16x2_pack_sat(f.mur, f.mug));
         g[kTile] = make_uint2(f16x2_pack_sat(f.mub, f.vc), f16x2_pack_sat(f.mud, f.vd));
     }
 }
@@ -377,6 +403,15 @@ __device__ __forceinline__ uint32_t fuse_list1(int fgc, int fgd, uint32_t fb) {
     return (fb & ~15u) | (uint32_t)F | ((uint32_t)(cpt + 3) << 1);
 }
 
+// Random bits for the weights of component i at padded pixel p when the
+// view asks for stochastic rounding, else 0.
+__device__ __forceinline__ uint32_t sr_weights(const CamView &cv, uint32_t p, int i) {
+    if (!(cv.flags & kStochasticWeights))
+        return 0u;
+    const uint32_t r = sr_bits(cv.tick, p, (uint32_t)i);
+    return r ? r : 1u;
+}
+
 // ------------------------------------------------------------ one pixel
 // p: padded linear pixel index (row * w_pad + x). Returns bit 0 fused label,
 // bit 1 colour foreground, bit 2 depth foreground (all 0 for padding).
@@ -437,7 +472,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
             const Fields f = {a[i].w, a[i].mu[0], a[i].mu[1], a[i].mu[2], a[i].v,
                               0.f,    a[i].mu[3], 0.f};
             if (PREC != 0 || cv.first)
-                store_fields<PREC, M, true>(plw, e0, tb, t, i, f);
+                store_fields<PREC, M, true, true>(plw, e0, tb, t, i, f, sr_weights(cv, p32, i));
             else
                 store_fields<PREC, M, false>(plw, e0, tb, t, i, f);
         }
@@ -521,7 +556,10 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
     for (int i = 0; i < M; ++i) {
         const Fields f = {c[i].w, c[i].mu[0], c[i].mu[1], c[i].mu[2], c[i].v,
                           d[i].w, d[i].mu[0], d[i].v};
-        store_fields<PREC, M>(plw, e0, tb, t, i, f);
+        if (kVariant == 0)
+            store_fields<PREC, M>(plw, e0, tb, t, i, f);
+        else
+            store_fields<PREC, M, true, true>(plw, e0, tb, t, i, f, sr_weights(cv, p32, i));
     }
     cv.fusion[p] = (uint8_t)fb;
     return (fb & 1u) | ((uint32_t)fgc << 1) | ((uint32_t)fgd << 2);

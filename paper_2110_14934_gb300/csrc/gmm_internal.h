@@ -90,7 +90,7 @@ cudaError_t pool_bank_release(int device, cudaStream_t s);
 __host__ __device__ inline int view_variant(const gmmdev::CamView &cv) {
     if (cv.flags & gmmdev::kModeAugmented)
         return 2;
-    return (cv.pc.flags | cv.pd.flags) ? 1 : 0;
+    return ((cv.pc.flags | cv.pd.flags) || (cv.flags & gmmdev::kStochasticWeights)) ? 1 : 0;
 }
 
 int num_sms();

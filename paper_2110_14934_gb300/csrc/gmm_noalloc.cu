@@ -63,6 +63,9 @@ extern "C" int gmm_apply_open3_noalloc(const gmm_config *cfg, void *state, int f
                                 "GMM_NOALLOC_MAX_MASK_WORDS (the fixed scratch size)");
     if (first != 0 && first != 1)
         return fail(GMM_EINVAL, "gmm_apply_open3_noalloc: first must be 0 or 1");
+    if (cfg->flags & GMM_FLAG_STOCHASTIC_WEIGHTS)
+        return fail(GMM_EINVAL, "gmm_apply_open3_noalloc: GMM_FLAG_STOCHASTIC_WEIGHTS needs a "
+                                "tick count (use a handle)");
     if (!state || reinterpret_cast<uintptr_t>(state) % 16)
         return fail(GMM_EINVAL, "gmm_apply_open3_noalloc: state must be non-NULL and 16-byte aligned");
     std::string p = check_frame_ptrs(rgb8, depth16, mask_out, nullptr, nullptr);
@@ -76,7 +79,7 @@ extern "C" int gmm_apply_open3_noalloc(const gmm_config *cfg, void *state, int f
         return rc;
     const Layout L = make_layout(cfg->H, cfg->W, cfg->M, cfg->precision);
     const gmmdev::CamView v = make_view(*cfg, L, state, rgb8, depth16, scratch, nullptr,
-                                        nullptr, first);
+                                        nullptr, first, 0u);
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = gmmhost::launch_tick(v, gmmhost::direct_threads(0, cfg->precision), s);
     if (e == cudaSuccess)

@@ -24,6 +24,7 @@ struct PoolCam {
     Layout L{};
     void *arena = nullptr;
     int initialized = 0;
+    uint32_t ticks = 0; // ticks taken (seeds stochastic rounding)
     bool submitted = false;
     const uint8_t *rgb = nullptr;
     const uint16_t *depth = nullptr;
@@ -290,7 +291,7 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
             continue;
         gmmhost::PoolArgs &a = p->h_args[b][li];
         a.views[j] = make_view(c.cfg, c.L, c.arena, c.rgb, c.depth, c.mask, c.fgr, c.fgd,
-                               c.initialized ? 0 : 1);
+                               c.initialized ? 0 : 1, c.ticks);
         all_variants = all_variants || gmmhost::view_variant(a.views[j]) != 0;
         a.tile_begin[j] = tiles;
         tiles += (c.L.n_pad + p->tile_pixels - 1) / p->tile_pixels;
@@ -329,6 +330,7 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         for (PoolCam &c : p->cams) {
             if (c.used && c.submitted) {
                 c.initialized = 1;
+                c.ticks += 1;
                 c.submitted = false;
             }
         }

@@ -87,7 +87,7 @@ def test_create_ex_rejects_bad_extensions():
                              ("morph_open", 2, "morph_open"), ("mode", 2, "mode"),
                              ("depth_scale", 0.0, "depth_scale"),
                              ("depth_scale", float("inf"), "depth_scale"),
-                             ("flags", 4, "flags")):
+                             ("flags", 8, "flags"), ("flags", 4, "needs GMM_PREC_F16")):
         c = G.GMMConfig.from_buffer_copy(cfg)
         setattr(c, field, val)
         assert not L.gmm_create_ex(ctypes.byref(c))

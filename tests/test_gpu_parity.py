@@ -286,3 +286,40 @@ def test_staged_variants_match_direct(H, W, M, prec):
         assert np.array_equal(g.planes(), ref.planes()), v
         assert np.array_equal(g.fusion(), ref.fusion()), v
         g.sync()  # also reports a pipeline wait that ran out
+
+
+@pytest.mark.parametrize("prec", [G.PREC_F32, G.PREC_F16])
+def test_large_frame_rows(prec):
+    """A frame near the size limit (11000 x 11001: 121 M padded pixels,
+    ragged rows; 11.6 GB of FP32 state), frames generated on the device. The
+    first, a middle and the last row must equal, bit for bit over four ticks,
+    the same rows run as 1-row cameras (pixels are independent; this checks
+    the large-index arithmetic against the small one), and in FP32 they must
+    match the oracle (free-running: pixels near a threshold at the
+    free-running margin are left out once flagged)."""
+    import torch
+    H, W, M, T = 11000, 11001, 3, 4
+    s = synth.scene(77, H, W, 1)
+    rgb_d, dep_d, _ = synth.frames_device(s, 0, T, with_gt=False)
+    g = G.GMM(H, W, M, precision=prec)
+    rows = [0, H // 2, H - 1]
+    host = [synth.rows_host(s, 0, T, y, 1) for y in rows]
+    small = [G.GMM(1, W, M, precision=prec) for _ in rows]
+    orcs = [O.OracleGMM(1, W, M, 0.01, 2.5, 0.7, 225.0, 0.05, eps=FREE_RUN_EPS) for _ in rows]
+    diverged = [np.zeros((1, W), bool) for _ in rows]
+    for t in range(T):
+        m = g.apply(rgb_d[t], dep_d[t])
+        torch.cuda.synchronize()
+        for k, y in enumerate(rows):
+            r1, d1 = to_dev(host[k][0][t], host[k][1][t])
+            m1 = small[k].apply(r1, d1)
+            torch.cuda.synchronize()
+            assert np.array_equal(words(m[y:y + 1]), words(m1)), (t, y)
+            if prec == G.PREC_F32:
+                o = orcs[k].tick(host[k][0][t], host[k][1][t])
+                diverged[k] |= o["near"] != 0
+                got = G.unpack_mask(words(m1), 1, W)
+                bad = (got != o["fused"].astype(bool)) & ~diverged[k]
+                assert not bad.any(), (t, y, int(bad.sum()))
+    del rgb_d, dep_d
+    g.close()

@@ -43,6 +43,10 @@
  *    ceil(W/32) uint32 words, 4-byte aligned; bit i of word c of row y is
  *    pixel x = 32*c + i (least significant bit first); bits for x >= W are 0.
  *  - A CUDA failure is sticky on the handle: later calls return GMM_ECUDA.
+ *  - Threads: a handle or a pool is used by one thread at a time (calls on
+ *    different handles and pools may run concurrently, and pools on one
+ *    device share their launch-argument bank safely); every gmm_server_*
+ *    call is thread-safe. Device work is ordered on the object's stream.
  */
 #ifndef GMM_H
 #define GMM_H

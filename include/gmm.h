@@ -45,8 +45,9 @@
  *  - A CUDA failure is sticky on the handle: later calls return GMM_ECUDA.
  *  - Threads: a handle or a pool is used by one thread at a time (calls on
  *    different handles and pools may run concurrently, and pools on one
- *    device share their launch-argument bank safely); every gmm_server_*
- *    call is thread-safe. Device work is ordered on the object's stream.
+ *    device share their launch-argument bank safely); the gmm_server_*
+ *    calls other than gmm_server_destroy may be made from any thread.
+ *    Device work is ordered on the object's stream.
  */
 #ifndef GMM_H
 #define GMM_H

@@ -395,7 +395,7 @@ int gmm_pool_autotune(gmm_pool_t *p, int iters, int *threads,
 /* Online tuning of the launch shape on real ticks: the next
  * ticks_per_shape x (number of candidates) calls of gmm_pool_tick each run
  * one candidate shape (block size 64/128/256, full or half residency, tiles
- * of 2048/8192/32768 pixels; round-robin, CUDA graphs off meanwhile), timed
+ * of 512/1024/2048/8192 pixels; round-robin, CUDA graphs off meanwhile), timed
  * by events on the pool's stream; once all have completed, the shape with
  * the lowest median tick time is kept and graph use restored. The ticks do
  * their normal work, so nothing is snapshotted. gmm_pool_set_launch during

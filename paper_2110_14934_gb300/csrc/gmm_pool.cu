@@ -117,7 +117,7 @@ static int blocks_for(const gmm_pool *p) {
 static std::vector<Shape> tuning_candidates(const gmm_pool *p) {
     std::vector<Shape> out;
     const int cand_threads[] = {64, 128, 256};
-    const int cand_tiles[] = {2048, 8192, 32768};
+    const int cand_tiles[] = {512, 1024, 2048, 8192};
     for (int t : cand_threads) {
         const int max_c = gmmhost::pool_max_ctas_per_sm(p->prec, t);
         const int cand_c[2] = {max_c, max_c > 1 ? max_c / 2 : 0};

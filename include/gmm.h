@@ -184,9 +184,10 @@ int gmm_wait_selftest(int timeout_ms, int *timed_out, double *waited_ms);
 /* Tick kernel of the handle (§IV: the per-pixel GPU pass). Both compute the
  * same arithmetic bit for bit. GMM_KERNEL_DIRECT (default): one thread per
  * pixel, coalesced loads and stores straight from and to HBM (always used
- * for the initialising tick); variant picks the CTA size (0, the default:
- * the measured best for the precision, 128 threads for FP32 and 32 for
- * FP16/BF16; 1..4: 256, 128, 64, 32 threads), ctas_per_sm is ignored.
+ * for the initialising tick; FP16/BF16 state: two pixels per thread);
+ * variant picks the CTA size (0, the default: the measured best for the
+ * precision, 128 threads for FP32 and 64 for FP16/BF16; 1..4: 256, 128, 64,
+ * 32 threads), ctas_per_sm is ignored.
  * GMM_KERNEL_STAGED: persistent CTAs stream tiles of the state through
  * shared memory with bulk copies in a multi-stage pipeline; variant picks
  * the depth (0..3: 2..5 stages of one 256-pixel tile each), ctas_per_sm the

@@ -13,16 +13,15 @@ namespace gmmhost {
 cudaError_t launch_tick(const gmmdev::CamView &cv, int threads, cudaStream_t s);
 
 // Block size of the direct tick kernel for gmm_set_kernel's variant: 0 the
-// measured best for the storage precision (FP32: 128, FP16/BF16: 32, one warp
-// per CTA, so a finished warp's slot is refilled at once), 1..4: 256, 128,
-// 64, 32.
+// measured best for the storage precision (FP32: 128; FP16/BF16: 64, two
+// warps of two pixels per thread), 1..4: 256, 128, 64, 32.
 inline int direct_threads(int variant, int prec) {
     switch (variant) {
     case 1: return 256;
     case 2: return 128;
     case 3: return 64;
     case 4: return 32;
-    default: return prec == 0 ? 128 : 32;
+    default: return prec == 0 ? 128 : 64;
     }
 }
 

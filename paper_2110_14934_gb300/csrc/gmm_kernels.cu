@@ -18,7 +18,8 @@ using gmmhost::PoolArgs;
 namespace {
 
 // ------------------------------------------------------------ single camera
-// One thread per padded pixel (n_pad is a multiple of 32: whole warps leave).
+// FP32 state: one thread per padded pixel (n_pad is a multiple of 32: whole
+// warps leave).
 template <int M, int PREC, int V>
 __device__ __forceinline__ void tick_body(const CamView &cv) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -28,25 +29,50 @@ __device__ __forceinline__ void tick_body(const CamView &cv) {
     write_mask_words(cv, p >> 5, bits);
 }
 
+// FP16/BF16 state: two pixels per thread, each warp a 64-pixel chunk (lane
+// t takes pixels t and t + 32, so both halves stay coalesced); the second
+// pixel's loads overlap the first one's arithmetic. A half chunk past n_pad
+// is skipped by the whole warp.
+template <int M, int PREC, int V>
+__device__ __forceinline__ void tick_body2(const CamView &cv) {
+    const int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 64;
+    if (base >= cv.n_pad)
+        return;
+    const int lane = threadIdx.x & 31;
+    uint32_t bits[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int64_t p = base + 32 * u + lane;
+        bits[u] = p < cv.n_pad ? process_pixel<M, PREC, PREC != 0, V>(cv, p) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (base + 32 * u < cv.n_pad)
+            write_mask_words(cv, (base >> 5) + u, bits[u]);
+}
+
 // FP32 state: HBM-bound; the register allocation without a residency hint
 // (64 registers) measured fastest. FP16/BF16 state: issue bound; at least
 // 1024 threads per SM. V: process_pixel's variant (the options are separate
 // instantiations, so the default kernels carry none of them). Small CTAs
-// (128 threads) measured faster than 256: a CTA's slot frees as soon as its
-// own 4 warps finish. A persistent grid-stride form measured slower (its loop
+// measured faster than 256 threads: a CTA's slot frees as soon as its own
+// warps finish. A persistent grid-stride form measured slower (its loop
 // costs registers: 66 in FP32, i.e. 3 CTAs of 256 per SM).
 template <int M, int V>
 __global__ void __launch_bounds__(256) k_tick_f32(const CamView cv) { tick_body<M, 0, V>(cv); }
 template <int M, int V>
-__global__ void __launch_bounds__(256, 4) k_tick_f16(const CamView cv) { tick_body<M, 1, V>(cv); }
+__global__ void __launch_bounds__(256, 4) k_tick_f16(const CamView cv) { tick_body2<M, 1, V>(cv); }
 
 template <int M, int PREC, int V>
 cudaError_t launch_tick_v(const CamView &cv, int threads, cudaStream_t s) {
-    const int64_t blocks = (cv.n_pad + threads - 1) / threads;
-    if (PREC == 0)
+    if (PREC == 0) {
+        const int64_t blocks = (cv.n_pad + threads - 1) / threads;
         k_tick_f32<M, V><<<(unsigned)blocks, threads, 0, s>>>(cv);
-    else
-        k_tick_f16<M, V><<<(unsigned)blocks, threads, 0, s>>>(cv);
+    } else {
+        const int64_t chunks = (cv.n_pad + 63) / 64; // one per warp
+        const int warps = threads / 32;
+        k_tick_f16<M, V><<<(unsigned)((chunks + warps - 1) / warps), threads, 0, s>>>(cv);
+    }
     return cudaGetLastError();
 }
 

@@ -92,6 +92,8 @@ struct gmm_pool {
     cudaGraphExec_t gexec[kStaging] = {};
     GraphSig gsig[kStaging];
     Tuning tune;
+    int occupancy[9] = {};  // resident pool CTAs per SM, by block size / 32
+    int sms = 0;
 };
 
 static void destroy_graphs(gmm_pool *p) {
@@ -103,14 +105,20 @@ static void destroy_graphs(gmm_pool *p) {
     }
 }
 
-static int blocks_for(const gmm_pool *p) {
+// Resident CTAs per SM of the pool kernel for a block size (queried once per
+// block size) times the SM count (queried once).
+static int blocks_for(gmm_pool *p) {
+    int &max_per_sm = p->occupancy[p->threads / 32];
+    if (max_per_sm == 0)
+        max_per_sm = gmmhost::pool_max_ctas_per_sm(p->prec, p->threads);
+    if (p->sms == 0)
+        p->sms = gmmhost::num_sms();
     int per_sm = p->ctas_per_sm;
-    const int max_per_sm = gmmhost::pool_max_ctas_per_sm(p->prec, p->threads);
     if (per_sm <= 0 || per_sm > max_per_sm)
         per_sm = max_per_sm;
     if (per_sm < 1)
         per_sm = 1;
-    return gmmhost::num_sms() * per_sm;
+    return p->sms * per_sm;
 }
 
 // Candidate launch shapes: block sizes, full or half residency, tile sizes.

@@ -422,21 +422,16 @@ def run_gmm(args, wl):
     rgb_d, dep_d, _ = synth.frames_device(scene, 0, nf, device=dev, with_gt=False)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
-    g = G.GMM(H, W, M, precision=prec, device=dev, flags=model_flags(args, G), **PARAMS)
+    # --morph: the handle runs the tick and the 3x3 opening of the fused mask
+    # back to back in every step (gmm_apply with morph_open = 1).
+    g = G.GMM(H, W, M, precision=prec, device=dev, flags=model_flags(args, G),
+              morph_open=args.morph, **PARAMS)
     g.set_kernel(KERNELS[args.kernel], args.variant, args.ctas)
     mask = g.new_mask()
     K, Wm = args.steps, args.warmup
-    # --morph: each step also runs the 3x3 opening of the fused mask (the
-    # tick writes a scratch mask, gmm_morph_open3 the output), with an event
-    # between the two launches to time each kernel.
-    tick_mask = g.new_mask() if args.morph else mask
 
-    def step(f, mid=None):
-        g.apply(rgb_d[f], dep_d[f], tick_mask, stream=stream)
-        if args.morph:
-            if mid is not None:
-                mid.record(stream)
-            G.morph_open3(tick_mask, mask, H, W, stream=stream)
+    def step(f):
+        g.apply(rgb_d[f], dep_d[f], mask, stream=stream)
 
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
@@ -446,20 +441,13 @@ def run_gmm(args, wl):
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    marks = ([(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(K)] if args.morph else None)
     barrier(world, dev)
     torch.cuda.synchronize()
     if clocks:
         clocks.start()
     t_start.record(stream)
     for k in range(K):
-        f = (Wm + k) % nf
-        if marks:
-            marks[k][0].record(stream)
-            step(f, marks[k][1])
-        else:
-            step(f)
+        step((Wm + k) % nf)
     t_end.record(stream)
     torch.cuda.synchronize()
     barrier(world, dev)
@@ -471,21 +459,46 @@ def run_gmm(args, wl):
 
     # Roofline of the tick kernel. Without --morph it is the only work in the
     # timed region (one launch per step, back to back on one stream), so its
-    # average launch duration is the region's event time over K; with --morph
-    # the events around each launch give both kernels' durations.
+    # average launch duration is the region's event time over K. With --morph
+    # a separate pass times a handle without the opening back to back (the
+    # tick's duration), then steps of tick + gmm_morph_open3 with events
+    # around the opening (its own duration; the events add a little to it).
     bpp = bytes_per_pixel(M, prec)
     morph_info = None
-    if marks:
-        tick_ms_sum = sum(a.elapsed_time(b) for a, b in marks)
-        ends_next = [marks[k + 1][0] for k in range(K - 1)] + [t_end]
-        morph_ms_sum = sum(marks[k][1].elapsed_time(ends_next[k]) for k in range(K))
-        avg_kernel_s = tick_ms_sum / K / 1e3
-        morph_s = morph_ms_sum / K / 1e3
+    if args.morph:
+        n_att = min(K, 2000)
+        solo = G.GMM(H, W, M, precision=prec, device=dev, flags=model_flags(args, G), **PARAMS)
+        solo.set_kernel(KERNELS[args.kernel], args.variant, args.ctas)
+        scratch = solo.new_mask()
+        for k in range(Wm):
+            solo.apply(rgb_d[k % nf], dep_d[k % nf], scratch, stream=stream)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for k in range(n_att):
+            f = (Wm + k) % nf
+            solo.apply(rgb_d[f], dep_d[f], scratch, stream=stream)
+        a1.record(stream)
+        marks = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_att)]
+        for k in range(n_att):
+            f = (Wm + k) % nf
+            solo.apply(rgb_d[f], dep_d[f], scratch, stream=stream)
+            marks[k][0].record(stream)
+            G.morph_open3(scratch, mask, H, W, stream=stream)
+            marks[k][1].record(stream)
+        torch.cuda.synchronize()
+        tick_s = a0.elapsed_time(a1) / n_att / 1e3
+        morph_s = sum(b.elapsed_time(c) for b, c in marks) / n_att / 1e3
+        solo.close()
+        avg_kernel_s = tick_s
         morph_bytes = 2 * H * G.mask_words_per_row(W) * 4
         morph_info = {"kernel": "k_morph_open3", "avg_us": morph_s * 1e6,
                       "algorithmic_bytes_per_launch": morph_bytes,
                       "achieved_gbs": morph_bytes / morph_s / 1e9,
-                      "share_of_step": morph_ms_sum / local_ms}
+                      "step_us_with_opening": local_ms / K * 1e3,
+                      "tick_alone_us": tick_s * 1e6,
+                      "opening_cost_us_per_step": local_ms / K * 1e3 - tick_s * 1e6,
+                      "attribution": f"{n_att} ticks alone back to back; {n_att} openings "
+                                     "between two events"}
     else:
         avg_kernel_s = local_ms / K / 1e3
     achieved = H * W * bpp / avg_kernel_s / 1e9

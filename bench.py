@@ -827,19 +827,25 @@ def run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, steps, warmup, 
 
 
 # ---------------------------------------------------------------- serving
-def serving_schedule(n_cams, duration, fps, session_s, live_fraction, seed):
+def serving_schedule(n_cams, duration, fps, session_s, live_fraction, seed, genlocked=False):
     """Seeded session and frame schedule: every camera alternates idle gaps
     and sessions, both exponential (Poisson joins and leaves), with mean
     session session_s and mean gap chosen for the given live fraction; a
     live camera offers frames every 1/fps s with +-2 ms uniform jitter.
-    Returns time-sorted events (t, kind, cam, k) with kind 0 = join,
-    1 = frame k of the session, 2 = leave."""
+    The cameras already live when the window opens joined at unrelated
+    earlier times, so each runs at its own phase (uniform in one frame
+    period); genlocked: they all run at phase 0 (a synchronised rig: their
+    frames arrive together, every period). Returns time-sorted events
+    (t, kind, cam, k) with kind 0 = join, 1 = frame k of the session,
+    2 = leave."""
     import numpy as np
-    rng = np.random.default_rng(seed)
+    rng = np.random.default_rng(seed)                # sessions
+    rng_t = np.random.default_rng([seed, 1])         # phases and jitter
     gap_s = session_s * (1.0 - live_fraction) / live_fraction
     ev = []
     for c in range(n_cams):
         live = rng.random() < live_fraction
+        phase = 0.0 if genlocked or not live else rng_t.uniform(0.0, 1.0 / fps)
         t = 0.0
         while t < duration:
             if live:
@@ -847,13 +853,14 @@ def serving_schedule(n_cams, duration, fps, session_s, live_fraction, seed):
                 ev.append((t, 0, c, 0))
                 k = 0
                 while True:
-                    tf = t + k / fps + rng.uniform(-0.002, 0.002)
+                    tf = t + phase + k / fps + rng_t.uniform(-0.002, 0.002)
                     if tf >= end:
                         break
                     ev.append((max(t, tf), 1, c, k))
                     k += 1
                 ev.append((end, 2, c, 0))
                 t = end
+                phase = 0.0
             else:
                 t += rng.exponential(gap_s)
             live = not live
@@ -861,7 +868,8 @@ def serving_schedule(n_cams, duration, fps, session_s, live_fraction, seed):
     return ev
 
 
-def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_depth=4):
+def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_depth=4,
+              genlocked=False):
     """Drive a Server through a seeded schedule in real time; returns stats."""
     import queue as pyqueue
 
@@ -869,7 +877,7 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
     srv = G.Server(budget_bytes=budget_bytes, precision=wl["prec"], max_cams=len(cams),
                    queue_depth=queue_depth)
     events = serving_schedule(len(cams), duration, wl["fps"], wl["session_frames"] / wl["fps"],
-                              wl["live_fraction"], seed)
+                              wl["live_fraction"], seed, genlocked)
     n_slot = queue_depth + 4
     # every camera's mask buffers, carved from one page-locked allocation made
     # before the clock starts (allocating page-locked memory in the loop
@@ -900,6 +908,10 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
     rt = th.Thread(target=releaser, daemon=True)
     rt.start()
     tickets, lag, admit_ms = [], [], []
+    # camera of each ticket (tickets count up from 0), allocated up front: a
+    # dict that grows in the real-time loop stalls it for tens of ms when it
+    # resizes
+    ticket_cam = np.full(sum(1 for e in events if e[1] == 1) + 1, -1, dtype=np.int32)
     # The cameras live when the window opens are admitted before the clock
     # starts (a server is up before it is measured); later joins are timed.
     n_initial = 0
@@ -914,6 +926,9 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
     import gc
     gc.disable()  # no collector pauses in the client's real-time loop
     t0 = srv.now() + 0.5
+    stalls = []  # events the client reached > 2 ms late, with the event before
+    slow_iters, waited = [], 0
+    prev = (None, 0.0)
     for (t, kind, c, k) in events[n_initial:]:
         due = t0 + t
         while True:
@@ -921,6 +936,10 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
             if d <= 0:
                 break
             time.sleep(d - 0.0005) if d > 0.001 else None
+        ti = srv.now()
+        if ti - due > 0.002 and len(stalls) < 20:
+            stalls.append({"t_s": round(t, 4), "kind": kind, "late_ms": round((ti - due) * 1e3, 3),
+                           "prev_kind": prev[0], "prev_call_ms": round(prev[1] * 1e3, 3)})
         H, W, M, _ = cams[c]
         if kind == 0:
             ta = time.perf_counter()
@@ -941,15 +960,26 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
             old = slot_ticket.get((c, slot))
             if old is not None and not srv.done(old):
                 srv.wait(old, 60000)
+                waited += 1
+            ts1 = srv.now()
             f = (k + c) % rgb_h.shape[0]
             lag.append((srv.now() - due) * 1e3)
             try:
+                ts2 = srv.now()
                 tk = srv.push(live[c], rgb_h[f], dep_h[f], masks[(c, slot)], t_arrival=due)
+                ts3 = srv.now()
+                if ts3 - ti > 0.005 and len(slow_iters) < 10:
+                    slow_iters.append({"t_s": round(t, 4), "slot_wait_ms": round((ts1 - ti) * 1e3, 3),
+                                       "index_ms": round((ts2 - ts1) * 1e3, 3),
+                                       "push_ms": round((ts3 - ts2) * 1e3, 3),
+                                       "ticket": tk, "ts2": ts2, "ts3": ts3})
                 tickets.append(tk)
+                ticket_cam[tk] = c
                 slot_ticket[(c, slot)] = tk
             except G.GMMError as e:
                 if e.code != G.EBUDGET:
                     raise
+        prev = (kind, srv.now() - ti)
     for tk in tickets:
         srv.wait(tk, 60000)
     t_end = srv.now()
@@ -960,10 +990,57 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
     rt.join()
     st = srv.stats()
     lat = np.sort(srv.latencies_ms())
+    trs = srv.traces()
+    parts = latency_breakdown(trs, ticket_cam, cams, t0)
+    for it in slow_iters:  # inside gmm_server_push: before / after its lock
+        row = trs[trs["ticket"] == it.pop("ticket")]
+        ts2, ts3 = it.pop("ts2"), it.pop("ts3")
+        if row.size:
+            it["to_lock_ms"] = round((float(row["t_pushed"][0]) - ts2) * 1e3, 3)
+            it["after_lock_ms"] = round((ts3 - float(row["t_pushed"][0])) * 1e3, 3)
+    if parts is not None:
+        parts["client_stalls"] = stalls[:3]
+        parts["client_slow_pushes"] = slow_iters
+        parts["client_slot_waits"] = waited
     srv.close()
     lag.sort()
     admit_ms.sort()
-    return st, lat, t_end - t0, lag, rel_err, admit_ms
+    return st, lat, t_end - t0, lag, rel_err, admit_ms, parts
+
+
+def latency_breakdown(tr, ticket_cam, cams, t0):
+    """Where the frames' latency went (from the engine's per-frame traces):
+    waiting to be batched (pushed -> taken into a tick), submission (taken
+    -> the tick's copies and launch queued), device (queued -> last download
+    seen complete); and the same split over the slowest 1% of frames. The
+    wait is split further into the client's lateness (arrival -> pushed)
+    and the engine's (pushed -> taken into a tick)."""
+    import numpy as np
+    if tr.size == 0:
+        return None
+    late = (tr["t_pushed"] - tr["t_arrival"]) * 1e3
+    wait = (tr["t_batched"] - tr["t_pushed"]) * 1e3
+    sub = (tr["t_submitted"] - tr["t_batched"]) * 1e3
+    dev = (tr["t_done"] - tr["t_submitted"]) * 1e3
+    tot = (tr["t_done"] - tr["t_arrival"]) * 1e3
+    tail = tot >= np.percentile(tot, 99)
+    px = np.array([H * W for (H, W, _, _) in cams] + [0])
+    res = px[ticket_cam[tr["ticket"]]]  # -1 (unknown) picks the trailing 0
+    q = lambda x, p: float(np.percentile(x, p))
+    win = np.floor((tr["t_arrival"][tail] - t0) / 0.1)  # 100 ms windows
+    return {"client_late_ms": {"p50": q(late, 50), "p99": q(late, 99), "max": float(late.max())},
+            "wait_ms": {"p50": q(wait, 50), "p99": q(wait, 99)},
+            "submit_ms": {"p50": q(sub, 50), "p99": q(sub, 99)},
+            "device_ms": {"p50": q(dev, 50), "p99": q(dev, 99)},
+            "tick_frames": {"p50": q(tr["tick_frames"], 50), "p99": q(tr["tick_frames"], 99)},
+            "slowest_1pct": {"frames": int(tail.sum()),
+                             "client_late_ms": float(late[tail].mean()),
+                             "wait_ms": float(wait[tail].mean()),
+                             "submit_ms": float(sub[tail].mean()),
+                             "device_ms": float(dev[tail].mean()),
+                             "tick_frames": float(tr["tick_frames"][tail].mean()),
+                             "share_1080p": float((res[tail] == 1920 * 1080).mean()),
+                             "windows_100ms": int(np.unique(win).size)}}
 
 
 def run_serving(args, wl):
@@ -987,14 +1064,21 @@ def run_serving(args, wl):
         ring.append((r.cpu().pin_memory(), d.cpu().pin_memory()))
     duration = args.serve_seconds or wl["duration_s"]
     barrier(world, dev)
-    st, lat, wall, lag, rel_err, admit_ms = serve_run(G, torch, cams, ring, wl,
+    st, lat, wall, lag, rel_err, admit_ms, parts = serve_run(G, torch, cams, ring, wl,
                                             int(wl["budget_gb"] * 1e9), duration, 2021 + rank)
     wall = reduce_max(wall, world, dev)
     pixels = st["pixels"]
     total_px = pixels * world  # weak scaling: every rank serves its own cameras
     value = total_px / wall / 1e6
-    st2, lat2, _, _, _, _ = serve_run(G, torch, cams, ring, wl, int(wl["tight_budget_gb"] * 1e9),
+    st2, lat2, _, _, _, _, _ = serve_run(G, torch, cams, ring, wl, int(wl["tight_budget_gb"] * 1e9),
                                    wl["tight_duration_s"], 77 + rank)
+    # a genlocked rig: the cameras live at the start deliver their frames
+    # together every period, so each period opens with one large burst
+    st3, lat3, _, _, _, _, parts3 = serve_run(G, torch, cams, ring, wl, int(wl["budget_gb"] * 1e9),
+                                              wl["tight_duration_s"], 2021 + rank, genlocked=True)
+    ev3 = serving_schedule(len(cams), wl["tight_duration_s"], wl["fps"],
+                           wl["session_frames"] / wl["fps"], wl["live_fraction"], 2021 + rank, True)
+    burst_px = sum(cams[c][0] * cams[c][1] for (t, kind, c, _) in ev3 if t == 0.0 and kind == 0)
     mean_bpp = sum(H * W * bytes_per_pixel(M, wl["prec"]) for (H, W, M, _) in cams) / \
         sum(H * W for (H, W, _, _) in cams)
     achieved = pixels * mean_bpp / wall / 1e9
@@ -1013,11 +1097,13 @@ def run_serving(args, wl):
             "latency_ms": {"p50": fnum(pct(list(lat), 50)), "p99": fnum(pct(list(lat), 99)),
                            "p999": fnum(pct(list(lat), 99.9)),
                            "max": float(lat[-1]) if lat.size else None,
-                           "what": "frame arrival to fused mask in host memory"},
+                           "what": "frame arrival to fused mask in host memory",
+                           "breakdown": parts},
             "serving": {"frames_completed": st["completed"], "frames_dropped": st["dropped"],
                         "sessions_admitted": st["admitted"], "admissions_rejected": st["rejected"],
                         "ticks": st["ticks"], "mean_frames_per_tick": st["completed"] / max(st["ticks"], 1),
-                        "driver_lag_ms_p99": fnum(pct(lag, 99)), "release_errors": len(rel_err),
+                        "driver_lag_ms_p99": fnum(pct(lag, 99)),
+                        "driver_lag_ms_max": fnum(lag[-1]) if lag else None, "release_errors": len(rel_err),
                         "admit_ms_p50": fnum(pct(admit_ms, 50)), "admit_ms_max":
                             fnum(admit_ms[-1]) if admit_ms else None,
                         "budget_gb": wl["budget_gb"]},
@@ -1025,6 +1111,13 @@ def run_serving(args, wl):
                              "sessions_admitted": st2["admitted"], "admissions_rejected": st2["rejected"],
                              "frames_completed": st2["completed"],
                              "latency_ms_p99": fnum(pct(list(lat2), 99))},
+            "genlocked": {"duration_s": wl["tight_duration_s"], "frames_completed": st3["completed"],
+                          "burst_mpx_at_start": burst_px / 1e6,
+                          "latency_ms": {"p50": fnum(pct(list(lat3), 50)),
+                                         "p99": fnum(pct(list(lat3), 99)),
+                                         "p999": fnum(pct(list(lat3), 99.9)),
+                                         "max": float(lat3[-1]) if lat3.size else None},
+                          "slowest_1pct": parts3["slowest_1pct"] if parts3 else None},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
                          "note": "offered-load bound: the cameras offer far less than the GPU "

@@ -485,6 +485,22 @@ int gmm_server_wait(gmm_server_t *s, long long ticket, int timeout_ms);
 int gmm_server_stats_get(gmm_server_t *s, gmm_server_stats *out);
 size_t gmm_server_latencies(gmm_server_t *s, float *ms_out, size_t n);
 
+/* Where a completed frame's latency went, on the gmm_server_now() clock
+ * (seconds): t_arrival as given to gmm_server_push; t_pushed when that call
+ * queued it; t_batched when the engine took the frame into a tick; t_submitted when that tick's uploads, launch and downloads
+ * were queued on the device; t_done when the engine saw the tick's last
+ * download complete (the latency's end). cam: the server's camera id;
+ * tick_frames: frames in the same tick. */
+typedef struct gmm_server_trace {
+    long long ticket;
+    int cam, tick_frames;
+    double t_arrival, t_pushed, t_batched, t_submitted, t_done;
+} gmm_server_trace;
+
+/* Copies up to n records, in completion order (the order of
+ * gmm_server_latencies), into out; returns how many were recorded. */
+size_t gmm_server_traces(gmm_server_t *s, gmm_server_trace *out, size_t n);
+
 /* Seconds on the engine's monotonic clock (the clock of t_arrival). */
 double gmm_server_now(void);
 

@@ -60,6 +60,13 @@ class ServerStats(ctypes.Structure):
                 ("used_bytes", ctypes.c_size_t)]
 
 
+class ServerTrace(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_longlong), ("cam", ctypes.c_int),
+                ("tick_frames", ctypes.c_int), ("t_arrival", ctypes.c_double),
+                ("t_pushed", ctypes.c_double), ("t_batched", ctypes.c_double), ("t_submitted", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 
@@ -130,6 +137,7 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_server_wait": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_int]),
         "gmm_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
         "gmm_server_latencies": (ctypes.c_size_t, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+        "gmm_server_traces": (ctypes.c_size_t, [_vp, ctypes.POINTER(ServerTrace), ctypes.c_size_t]),
         "gmm_server_now": (ctypes.c_double, []),
         "gmm_server_destroy": (ctypes.c_int, [_vp, ctypes.c_int]),
     }
@@ -493,6 +501,17 @@ class Server:
         if n:
             L.gmm_server_latencies(self._s, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n)
         return out
+
+    def traces(self) -> np.ndarray:
+        """Per completed frame, in completion order: ticket, camera, frames in
+        its tick, and the arrival / pushed / batched / submitted / done times
+        (seconds, gmm_server_now clock)."""
+        L = load_library()
+        n = int(L.gmm_server_traces(self._s, None, 0))
+        buf = (ServerTrace * max(n, 1))()
+        if n:
+            n = int(min(n, L.gmm_server_traces(self._s, buf, n)))
+        return np.ctypeslib.as_array(buf)[:n].copy()
 
     def close(self, timeout_ms: int = 60000) -> None:
         if getattr(self, "_s", None):

@@ -6,10 +6,10 @@
 // copies of one tick overlap the compute of its neighbours.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
-#include <cstring>
 #include <deque>
 #include <mutex>
 #include <new>
@@ -38,6 +38,8 @@ struct Frame {
     const uint16_t *depth;
     uint32_t *mask;
     double t_arrival;
+    double t_pushed = 0.0;  // gmm_server_push queued it
+    double t_batched = 0.0; // the engine took it into a tick
 };
 
 struct SrvCam {
@@ -52,6 +54,7 @@ struct SrvCam {
 
 struct TickRec {
     cudaEvent_t done = nullptr;
+    double t_submitted = 0.0; // copies and launch queued
     std::vector<std::pair<int, Frame>> jobs;
 };
 
@@ -70,9 +73,12 @@ struct gmm_server {
     std::condition_variable cv_work, cv_done;
     std::thread engine;
     std::atomic<bool> stop{false}, abort_now{false};
-    std::vector<signed char> done; // per ticket: 0 pending, 1 done, -1 failed
+    // Per-ticket and per-frame records grow in chunks (no reallocation
+    // copies a growing array while the lock that pushes need is held).
+    std::deque<signed char> done; // per ticket: 0 pending, 1 done, -1 failed
     long long next_ticket = 0;
-    std::vector<float> lat_ms;
+    std::deque<float> lat_ms;
+    std::deque<gmm_server_trace> traces; // parallel to lat_ms
     gmm_server_stats st{};
     cudaError_t sticky = cudaSuccess;
     // engine thread only
@@ -89,6 +95,9 @@ static void finish_tick(gmm_server *s, TickRec &t, bool ok) {
             c.in_flight = false;
             if (ok) {
                 s->lat_ms.push_back((float)((tnow - j.second.t_arrival) * 1e3));
+                s->traces.push_back(gmm_server_trace{j.second.ticket, j.first, (int)t.jobs.size(),
+                                                     j.second.t_arrival, j.second.t_pushed,
+                                                     j.second.t_batched, t.t_submitted, tnow});
                 s->done[(size_t)j.second.ticket] = 1;
                 s->st.completed += 1;
                 s->st.pixels += (long long)c.cfg.H * c.cfg.W;
@@ -173,10 +182,12 @@ static void engine_main(gmm_server *s) {
         bool quit = false;
         {
             std::unique_lock<std::mutex> lk(s->mu);
+            const double tb = clock_s();
             for (size_t i = 0; i < s->cams.size(); ++i) {
                 SrvCam &c = s->cams[i];
                 if (c.used && !c.in_flight && !c.queue.empty()) {
                     t.jobs.emplace_back((int)i, c.queue.front());
+                    t.jobs.back().second.t_batched = tb;
                     c.queue.pop_front();
                     c.in_flight = true;
                 }
@@ -212,6 +223,7 @@ static void engine_main(gmm_server *s) {
             finish_tick(s, t, false);
             continue;
         }
+        t.t_submitted = clock_s();
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->st.ticks += 1;
@@ -403,7 +415,7 @@ long long gmm_server_push(gmm_server_t *s, int cam, const uint8_t *rgb8_host,
     }
     const long long t = s->next_ticket++;
     s->done.push_back(0);
-    c.queue.push_back(Frame{t, rgb8_host, depth16_host, mask_host, t_arrival});
+    c.queue.push_back(Frame{t, rgb8_host, depth16_host, mask_host, t_arrival, clock_s()});
     s->st.pushed += 1;
     s->cv_work.notify_one();
     return t;
@@ -448,8 +460,18 @@ size_t gmm_server_latencies(gmm_server_t *s, float *ms_out, size_t n) {
     std::lock_guard<std::mutex> lk(s->mu);
     const size_t k = n < s->lat_ms.size() ? n : s->lat_ms.size();
     if (ms_out && k)
-        std::memcpy(ms_out, s->lat_ms.data(), k * sizeof(float));
+        std::copy(s->lat_ms.begin(), s->lat_ms.begin() + (std::ptrdiff_t)k, ms_out);
     return s->lat_ms.size();
+}
+
+size_t gmm_server_traces(gmm_server_t *s, gmm_server_trace *out, size_t n) {
+    if (!s)
+        return 0;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const size_t k = n < s->traces.size() ? n : s->traces.size();
+    if (out && k)
+        std::copy(s->traces.begin(), s->traces.begin() + (std::ptrdiff_t)k, out);
+    return s->traces.size();
 }
 
 int gmm_server_destroy(gmm_server_t *s, int timeout_ms) {

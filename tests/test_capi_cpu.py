@@ -142,3 +142,17 @@ def test_server_host_checks():
     t0 = L.gmm_server_now()
     t1 = L.gmm_server_now()
     assert t1 >= t0 > 0
+
+
+def test_server_trace_struct_matches_header():
+    """The ctypes mirror of gmm_server_trace lists the header's fields in
+    order, with C's layout (56 bytes, no padding)."""
+    text = open(os.path.join(ROOT, "include", "gmm.h")).read()
+    body = text[text.index("typedef struct gmm_server_trace {"):text.index("} gmm_server_trace;")]
+    names = []
+    for decl in re.findall(r"^\s*(?:long long|int|double)\s+([^;]+);", body, re.M):
+        names += [n.strip() for n in decl.split(",")]
+    assert names == [f[0] for f in G.ServerTrace._fields_]
+    assert ctypes.sizeof(G.ServerTrace) == 56
+    L = G.load_library()
+    assert L.gmm_server_traces(None, None, 0) == 0

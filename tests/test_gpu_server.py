@@ -61,6 +61,16 @@ def test_server_results_equal_alone_in_a_changing_mix(prec):
     assert st["completed"] == len(order) and st["dropped"] == 0 and st["ticks"] >= n
     lat = srv.latencies_ms()
     assert lat.size == len(order) and np.all(lat > 0) and np.all(lat < 30000)
+    # the traces: one per completed frame, in the same order, times in order
+    tr = srv.traces()
+    assert tr.size == lat.size
+    assert sorted(tr["ticket"].tolist()) == sorted(tickets)
+    assert np.all(tr["t_arrival"] <= tr["t_pushed"]) and np.all(tr["t_pushed"] <= tr["t_batched"])
+    assert np.all(tr["t_batched"] <= tr["t_submitted"])
+    assert np.all(tr["t_submitted"] <= tr["t_done"])
+    assert np.allclose((tr["t_done"] - tr["t_arrival"]) * 1e3, lat, rtol=1e-5, atol=1e-3)
+    assert np.all((tr["tick_frames"] >= 1) & (tr["tick_frames"] <= len(CAMS)))
+    assert set(tr["cam"].tolist()) == set(ids)
     srv.close()
 
 

@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.run(["nvcc", "-shared", f"-gencode=arch=compute_{ARCH},code=sm_{ARCH}", "-o", tmp]
-                   + objs, check=True)
+                   + objs + ["-ldl"], check=True)
     os.replace(tmp, LIB)
     for o in objs:
         os.remove(o)

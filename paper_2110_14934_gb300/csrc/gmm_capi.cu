@@ -500,6 +500,7 @@ int gmm_set_stream(gmm_t *h, void *stream) {
 
 int gmm_apply_ex(gmm_t *h, const uint8_t *rgb8, const uint16_t *depth16, uint32_t *mask_out,
                  uint32_t *fg_rgb_out, uint32_t *fg_d_out) {
+    TraceRange tr("gmm_apply");
     if (!h)
         return fail(GMM_EINVAL, "gmm_apply: null handle");
     if (h->sticky != cudaSuccess)
@@ -550,6 +551,7 @@ static int ensure_pipe(gmm_ctx *h) {
 
 long long gmm_pipe_submit(gmm_t *h, const uint8_t *rgb8_host, const uint16_t *depth16_host,
                           uint32_t *mask_host) {
+    TraceRange tr("gmm_pipe_submit");
     if (!h)
         return fail(GMM_EINVAL, "gmm_pipe_submit: null handle");
     if (h->sticky != cudaSuccess)

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -15,6 +16,16 @@ extern thread_local std::string g_err;
 
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t *sticky, cudaError_t e, const char *what);
+
+// An NVTX range over the scope (one per host entry point that queues a
+// tick), so profilers can group each tick's launches and copies; without a
+// profiler attached it costs one predictable branch.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Makes `dev` current for the scope and restores the caller's device.
 struct DeviceGuard {

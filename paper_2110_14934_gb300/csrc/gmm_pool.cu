@@ -494,6 +494,7 @@ int gmm_pool_inject_cuda_error(gmm_pool_t *p, int cuda_error) {
 }
 
 int gmm_pool_tick(gmm_pool_t *p) {
+    TraceRange tr("gmm_pool_tick");
     if (!p)
         return fail(GMM_EINVAL, "gmm_pool_tick: null pool");
     if (p->sticky != cudaSuccess)

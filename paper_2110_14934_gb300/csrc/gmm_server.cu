@@ -131,6 +131,7 @@ static void harvest(gmm_server *s, bool block) {
 }
 
 static cudaError_t enqueue_tick(gmm_server *s, TickRec &t) {
+    TraceRange tr("gmm_server tick");
     cudaError_t e = cudaSuccess;
     for (auto &j : t.jobs) {
         SrvCam &c = s->cams[j.first];

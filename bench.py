@@ -74,6 +74,10 @@ TRAFFIC_RECORDS = {
     ("tick", 1): ("gmm_tick_f16_m5_1920x1080.md", ("gmm_device.cuh", "gmm_kernels.cu"), ""),
     ("pool", 0): ("gmm_pool_tick_mixed_cameras.md", ("gmm_device.cuh", "gmm_pool_kernel.cu"), "_f32"),
     ("pool", 1): ("gmm_pool_tick_mixed_cameras.md", ("gmm_device.cuh", "gmm_pool_kernel.cu"), "_f16"),
+    ("pool_flat", 0): ("gmm_pool_tick_mixed_cameras.md", ("gmm_device.cuh", "gmm_pool_kernel.cu"),
+                       "_flat_f32"),
+    ("pool_flat", 1): ("gmm_pool_tick_mixed_cameras.md", ("gmm_device.cuh", "gmm_pool_kernel.cu"),
+                       "_flat_f16"),
 }
 KERNEL_SOURCES = [os.path.join(CSRC, f) for f in TRAFFIC_RECORDS[("tick", 0)][1]]
 
@@ -659,7 +663,10 @@ def run_pool(args, wl):
     submit(0)
     pool.tick(stream)  # frame 0 initialises every model
     k = 1
-    if not args.no_autotune:
+    if args.pool_launch:
+        pool.set_launch(*[int(v) for v in args.pool_launch.split(",")])
+        shape = pool.tuning()[1]
+    elif not args.no_autotune:
         # online tuning: the first warm-up ticks of the sequence try each
         # candidate launch shape (3 ticks each) and the pool keeps the best
         pool.autotune_online(3)
@@ -702,7 +709,9 @@ def run_pool(args, wl):
     tick_bytes = sum(H * W * bytes_per_pixel(M, prec) for (H, W, M, _) in cams)
     achieved = tick_bytes / (local_ms / K / 1e3) / 1e9
     # one launch per tick up to 128 cameras (more: a launch per 128)
-    traffic = recorded_traffic("pool", prec, tick_bytes) if len(cams) <= 128 else None
+    flat = bool(shape) and shape.get("ctas_per_sm", 0) < 0
+    traffic = (recorded_traffic("pool_flat" if flat else "pool", prec, tick_bytes)
+               if len(cams) <= 128 else None)
     peak, peak_src = measured_hbm_peak()
 
     # per-tick device latency
@@ -760,7 +769,7 @@ def run_pool(args, wl):
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                          "traffic_note": "scaled from an 8-camera capture by algorithmic bytes",
                          "algorithmic_bytes_per_tick": tick_bytes,
-                         "kernel": f"k_pool_tick<{'f32' if prec == 0 else 'f16'}>"},
+                         "kernel": f"k_pool_{'flat' if flat else 'tick'}<{'f32' if prec == 0 else 'f16'}>"},
             "plain_one_camera_per_launch_f32": {"value": plain_value, "unit": UNIT,
                                                 "steps": n_plain,
                                                 "pooled_over_plain": value / plain_value},
@@ -1239,6 +1248,9 @@ def main(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=0.0,
                     help="serving workload: simulated seconds (0: the workload's 20)")
     ap.add_argument("--no-autotune", action="store_true", help="pooled workloads: default launch")
+    ap.add_argument("--pool-launch", default="",
+                    help="pooled workloads: THREADS,CTAS_PER_SM,TILE_PIXELS instead of tuning "
+                         "(CTAS_PER_SM -1: the flat form)")
     ap.add_argument("--frames", type=int, default=0,
                     help="resident frames to cycle through (0: the workload's sequence length)")
     ap.add_argument("--stochastic-weights", action="store_true",

@@ -379,9 +379,13 @@ int gmm_pool_inject_cuda_error(gmm_pool_t *p, int cuda_error);
 
 int gmm_pool_set_stream(gmm_pool_t *p, void *cuda_stream);
 
-/* Launch shape of the persistent kernel: threads per block (64..256, a
- * multiple of 32), CTAs per SM (>= 1), pixels per tile (a multiple of the
- * block size). 0 keeps the current value. */
+/* Launch shape of the pooled kernel: threads per block (64..256, a
+ * multiple of 32); CTAs per SM of the persistent form (>= 1; its CTAs loop
+ * over tiles of tile_pixels pixels, a multiple of the block size), or -1
+ * for the flat form (a grid over the launch's pixels in which every warp
+ * takes one chunk of 32 pixels, FP32, or 64, FP16/BF16, and exits;
+ * tile_pixels is then unused). 0 keeps the current value (initially: 128
+ * threads, as many persistent CTAs as fit, 2048-pixel tiles). */
 int gmm_pool_set_launch(gmm_pool_t *p, int threads, int ctas_per_sm,
                         int tile_pixels);
 
@@ -395,8 +399,9 @@ int gmm_pool_autotune(gmm_pool_t *p, int iters, int *threads,
 
 /* Online tuning of the launch shape on real ticks: the next
  * ticks_per_shape x (number of candidates) calls of gmm_pool_tick each run
- * one candidate shape (block size 64/128/256, full or half residency, tiles
- * of 512/1024/2048/8192 pixels; round-robin, CUDA graphs off meanwhile), timed
+ * one candidate shape (block size 64/128/256; the persistent form at full or
+ * half residency with tiles of 512/1024/2048/8192 pixels, and the flat form;
+ * round-robin, CUDA graphs off meanwhile), timed
  * by events on the pool's stream; once all have completed, the shape with
  * the lowest median tick time is kept and graph use restored. The ticks do
  * their normal work, so nothing is snapshotted. gmm_pool_set_launch during

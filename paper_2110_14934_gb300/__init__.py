@@ -386,6 +386,8 @@ class Pool:
         _check(load_library().gmm_pool_set_stream(self._p, _stream_ptr(stream, self.device)))
 
     def set_launch(self, threads=0, ctas_per_sm=0, tile_pixels=0) -> None:
+        """Launch shape: block size; persistent CTAs per SM and tile size, or
+        ctas_per_sm=-1 for the flat form (one chunk per warp). 0 keeps."""
         _check(load_library().gmm_pool_set_launch(self._p, threads, ctas_per_sm, tile_pixels))
 
     def autotune(self, iters=3):

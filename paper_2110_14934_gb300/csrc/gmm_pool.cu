@@ -34,19 +34,23 @@ struct PoolCam {
 // What a captured graph depends on. The views and tile tables are read at
 // replay from the page-locked staging buffer the graph was captured with.
 struct GraphSig {
-    int n_launch = -1, threads = 0, blocks = 0;
-    bool all_variants = false;
+    int n_launch = -1, threads = 0;
+    std::vector<int> blocks; // per launch
+    bool all_variants = false, flat = false;
     bool operator==(const GraphSig &o) const {
         return n_launch == o.n_launch && threads == o.threads && blocks == o.blocks &&
-               all_variants == o.all_variants;
+               all_variants == o.all_variants && flat == o.flat;
     }
 };
 
 constexpr int kStaging = 2; // page-locked argument buffers, used alternately
 
+// ctas < 0: the flat (non-persistent) form; tile is then its chunk size.
 struct Shape {
     int threads, ctas, tile;
 };
+
+int chunk_pixels(int prec) { return prec == 0 ? 32 : 64; }
 
 // Online tuning: real ticks cycle through candidate launch shapes, each tick
 // timed by an event pair on the pool's stream; when every candidate has run
@@ -78,7 +82,7 @@ struct gmm_pool {
     cudaStream_t cap_stream = nullptr; // graph capture (the legacy stream cannot capture)
     cudaMemPool_t mempool = nullptr;   // cameras' state; keeps freed memory mapped
     cudaError_t sticky = cudaSuccess;
-    int threads = 128, ctas_per_sm = 0, tile_pixels = 2048;
+    int threads = 128, ctas_per_sm = 0, tile_pixels = 2048; // ctas_per_sm < 0: flat form
     // Tile counters, two sets of kmax (one per launch of a tick): a tick
     // uses set `parity` and its launches zero the other set for the next.
     int *d_counters = nullptr;
@@ -121,7 +125,8 @@ static int blocks_for(gmm_pool *p) {
     return p->sms * per_sm;
 }
 
-// Candidate launch shapes: block sizes, full or half residency, tile sizes.
+// Candidate launch shapes: block sizes; the persistent form at full or half
+// residency with each tile size, and the flat form.
 static std::vector<Shape> tuning_candidates(const gmm_pool *p) {
     std::vector<Shape> out;
     const int cand_threads[] = {64, 128, 256};
@@ -133,6 +138,7 @@ static std::vector<Shape> tuning_candidates(const gmm_pool *p) {
             if (c >= 1)
                 for (int tp : cand_tiles)
                     out.push_back({t, c, tp});
+        out.push_back({t, -1, chunk_pixels(p->prec)});
     }
     return out;
 }
@@ -189,32 +195,34 @@ static int tuning_poll(gmm_pool *p, bool block) {
 
 // Enqueue the tick's launches (argument upload + persistent kernel each)
 // from staging buffer b.
-static cudaError_t enqueue_body(gmm_pool *p, cudaStream_t s, int b, int n_launch, int blocks,
-                                bool all_variants) {
+static cudaError_t enqueue_body(gmm_pool *p, cudaStream_t s, int b, const GraphSig &sig) {
     cudaError_t e = cudaSuccess;
-    for (int li = 0; li < n_launch && e == cudaSuccess; ++li)
-        e = gmmhost::launch_pool_tick_impl(&p->h_args[b][li], p->threads, blocks, p->prec,
-                                           all_variants, s);
+    for (int li = 0; li < sig.n_launch && e == cudaSuccess; ++li)
+        e = gmmhost::launch_pool_tick_impl(&p->h_args[b][li], sig.threads, sig.blocks[li],
+                                           p->prec, sig.all_variants, sig.flat, s);
     return e;
 }
 
 // Launch the tick, directly or by replaying the graph captured for staging
 // buffer b (captured again when its shape changed).
 static cudaError_t launch_tick(gmm_pool *p, int b, int n_launch, bool all_variants) {
-    const int blocks = blocks_for(p);
+    GraphSig sig;
+    sig.n_launch = n_launch;
+    sig.threads = p->threads;
+    sig.all_variants = all_variants;
+    sig.flat = p->ctas_per_sm < 0;
+    const int warps = p->threads / 32;
+    for (int li = 0; li < n_launch; ++li) // flat: one warp per chunk
+        sig.blocks.push_back(sig.flat ? (int)((p->h_args[b][li].n_tiles + warps - 1) / warps)
+                                      : blocks_for(p));
     if (!p->use_graph) {
         cudaError_t e = gmmhost::pool_bank_acquire(p->device, p->stream);
         if (e != cudaSuccess)
             return e;
-        e = enqueue_body(p, p->stream, b, n_launch, blocks, all_variants);
+        e = enqueue_body(p, p->stream, b, sig);
         const cudaError_t er = gmmhost::pool_bank_release(p->device, p->stream);
         return e != cudaSuccess ? e : er;
     }
-    GraphSig sig;
-    sig.n_launch = n_launch;
-    sig.threads = p->threads;
-    sig.blocks = blocks;
-    sig.all_variants = all_variants;
     cudaError_t e = cudaSuccess;
     if (!(p->gexec[b] && p->gsig[b] == sig)) {
         if (p->gexec[b])
@@ -224,8 +232,7 @@ static cudaError_t launch_tick(gmm_pool *p, int b, int n_launch, bool all_varian
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const cudaError_t eb = enqueue_body(p, p->cap_stream, b, n_launch, blocks,
-                                                all_variants);
+            const cudaError_t eb = enqueue_body(p, p->cap_stream, b, sig);
             e = cudaStreamEndCapture(p->cap_stream, &g);
             if (eb != cudaSuccess)
                 e = eb;
@@ -276,6 +283,8 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
             return rc;
     }
     // The launches' arguments: up to kPoolViews cameras each.
+    // tiles, or in the flat form one chunk per warp
+    const int unit = p->ctas_per_sm < 0 ? chunk_pixels(p->prec) : p->tile_pixels;
     int *cur = p->d_counters + p->parity * p->kmax;
     int *next = p->d_counters + (1 - p->parity) * p->kmax;
     int li = 0, j = 0;
@@ -286,7 +295,7 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         a.tile_begin[j] = tiles;
         a.n_jobs = j;
         a.n_tiles = tiles;
-        a.tile_pixels = p->tile_pixels;
+        a.tile_pixels = unit;
         a.counter = cur + li;
         a.reset = next;
         a.n_reset = p->kmax;
@@ -302,7 +311,7 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
                                c.initialized ? 0 : 1, c.ticks);
         all_variants = all_variants || gmmhost::view_variant(a.views[j]) != 0;
         a.tile_begin[j] = tiles;
-        tiles += (c.L.n_pad + p->tile_pixels - 1) / p->tile_pixels;
+        tiles += (c.L.n_pad + unit - 1) / unit;
         if (++j == gmmhost::kPoolViews)
             close_launch();
     }
@@ -518,12 +527,13 @@ int gmm_pool_set_launch(gmm_pool_t *p, int threads, int ctas_per_sm, int tile_pi
         return fail(GMM_EINVAL, "gmm_pool_set_launch: null pool");
     const int t = threads ? threads : p->threads;
     const int c = ctas_per_sm ? ctas_per_sm : p->ctas_per_sm;
-    const int tp = tile_pixels ? tile_pixels : p->tile_pixels;
+    // leaving the flat form without a tile size: the default tile
+    const int tp = tile_pixels ? tile_pixels : (c >= 0 && p->ctas_per_sm < 0) ? 2048 : p->tile_pixels;
     if (t < 64 || t > 256 || t % 32)
         return fail(GMM_EINVAL, "gmm_pool_set_launch: threads must be 64..256, a multiple of 32");
-    if (c < 0 || c > 32)
-        return fail(GMM_EINVAL, "gmm_pool_set_launch: ctas_per_sm must be in [0, 32]");
-    if (tp < t || tp % t || tp > (1 << 24))
+    if (c < -1 || c > 32)
+        return fail(GMM_EINVAL, "gmm_pool_set_launch: ctas_per_sm must be in [-1, 32]");
+    if (c >= 0 && (tp < t || tp % t || tp > (1 << 24)))
         return fail(GMM_EINVAL, "gmm_pool_set_launch: tile_pixels must be a multiple of threads");
     p->threads = t;
     p->ctas_per_sm = c;

@@ -1,7 +1,8 @@
-// Multi-camera persistent tick: one launch advances every camera of a pool
-// that has a submitted frame (up to kPoolViews cameras per launch), with the
-// per-pixel arithmetic of the single-camera kernel (gmm_device.cuh), and the
-// per-device argument bank its launches share.
+// Multi-camera tick: one launch advances every camera of a pool that has a
+// submitted frame (up to kPoolViews cameras per launch), with the per-pixel
+// arithmetic of the single-camera kernel (gmm_device.cuh), in a persistent
+// form (CTAs loop over tiles) or a flat one (one chunk per warp); and the
+// per-device argument bank their launches share.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -86,6 +87,73 @@ __global__ void __launch_bounds__(256, PREC == 0 ? 3 : 4) k_pool_tick() {
     }
 }
 
+// Non-persistent form: every warp takes one chunk of the launch's implicit
+// chunk list (tile_begin counts chunks here: 32 pixels in FP32, one per lane;
+// 64 in FP16/BF16, two per lane with the second pixel's loads overlapping
+// the first one's arithmetic, as in the single-camera kernels) and finds its
+// camera by binary search. No counter and no loop: a CTA's slot frees as soon
+// as its own warps finish, and no registers carry a loop across pixels.
+template <int M, int PREC, int V>
+__device__ __forceinline__ void flat_chunk(const CamView &cv, int64_t base) {
+    const int lane = threadIdx.x & 31;
+    if (PREC == 0) { // n_pad is a multiple of 32: the chunk is whole
+        const int64_t p = base + lane;
+        write_mask_words(cv, p >> 5, process_pixel<M, PREC, true, V>(cv, p));
+        return;
+    }
+    uint32_t bits[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int64_t p = base + 32 * u + lane;
+        bits[u] = p < cv.n_pad ? process_pixel<M, PREC, true, V>(cv, p) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (base + 32 * u < cv.n_pad)
+            write_mask_words(cv, (base >> 5) + u, bits[u]);
+}
+
+template <int M, int PREC, bool kAll>
+__device__ __forceinline__ void flat_chunk_v(const CamView &cv, int64_t base) {
+    if (!kAll) {
+        flat_chunk<M, PREC, 0>(cv, base);
+        return;
+    }
+    switch (gmmhost::view_variant(cv)) {
+    case 0: flat_chunk<M, PREC, 0>(cv, base); break;
+    case 1: flat_chunk<M, PREC, 1>(cv, base); break;
+    default: flat_chunk<M, PREC, 2>(cv, base); break;
+    }
+}
+
+// FP32: no residency hint (76 registers, no spills; held to 64 it spills and
+// measured slower). FP16/BF16: 64 registers, as in the other kernels.
+template <int PREC, bool kAll>
+__global__ void __launch_bounds__(256, PREC == 0 ? 1 : 4) k_pool_flat() {
+    const PoolArgs &a = c_pool;
+    if (blockIdx.x == 0) // the next tick's counters, as the persistent form does
+        for (int i = threadIdx.x; i < a.n_reset; i += blockDim.x)
+            a.reset[i] = 0;
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= a.n_tiles)
+        return;
+    int lo = 0, hi = a.n_jobs - 1;
+    while (lo < hi) { // last job with tile_begin <= c (uniform across the warp)
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.tile_begin[mid] <= c)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const CamView &cv = a.views[lo];
+    const int64_t base = (c - a.tile_begin[lo]) * a.tile_pixels;
+    switch (cv.M) {
+    case 3: flat_chunk_v<3, PREC, kAll>(cv, base); break;
+    case 4: flat_chunk_v<4, PREC, kAll>(cv, base); break;
+    default: flat_chunk_v<5, PREC, kAll>(cv, base); break;
+    }
+}
+
 } // namespace
 
 namespace gmmhost {
@@ -124,12 +192,21 @@ cudaError_t pool_bank_release(int device, cudaStream_t s) {
 }
 
 cudaError_t launch_pool_tick_impl(const PoolArgs *args_host, int threads, int blocks, int prec,
-                                  bool all_variants, cudaStream_t s) {
+                                  bool all_variants, bool flat, cudaStream_t s) {
     cudaError_t e = cudaMemcpyToSymbolAsync(c_pool, args_host, sizeof(PoolArgs), 0,
                                             cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess)
         return e;
-    if (prec == 0 && !all_variants)
+    if (flat) {
+        if (prec == 0 && !all_variants)
+            k_pool_flat<0, false><<<blocks, threads, 0, s>>>();
+        else if (prec == 0)
+            k_pool_flat<0, true><<<blocks, threads, 0, s>>>();
+        else if (!all_variants)
+            k_pool_flat<1, false><<<blocks, threads, 0, s>>>();
+        else
+            k_pool_flat<1, true><<<blocks, threads, 0, s>>>();
+    } else if (prec == 0 && !all_variants)
         k_pool_tick<0, false><<<blocks, threads, 0, s>>>();
     else if (prec == 0)
         k_pool_tick<0, true><<<blocks, threads, 0, s>>>();

@@ -19,12 +19,12 @@ def _frames(n):
     return [scene_frames(500 + i, H, W, i % 2, 0, n) for i, (H, W, M) in enumerate(CAMS)]
 
 
-def _alone(frames, schedule):
+def _alone(frames, schedule, precision=G.PREC_F32):
     """Each camera in its own handle, fed only on the ticks it is scheduled."""
     import torch
     out = {}
     for i, (H, W, M) in enumerate(CAMS):
-        g = G.GMM(H, W, M)
+        g = G.GMM(H, W, M, precision=precision)
         k = 0
         for t, active in enumerate(schedule):
             if i in active:
@@ -88,14 +88,33 @@ def test_pool_equals_alone_in_a_changing_mix():
         assert np.array_equal(a[key], b[key]), key
 
 
+def _valid_shape(shape):
+    """A persistent shape (tiles a multiple of the block) or the flat form."""
+    return shape["threads"] in (64, 128, 256) and (
+        shape["ctas_per_sm"] == -1 or shape["tile_pixels"] % shape["threads"] == 0)
+
+
 @pytest.mark.parametrize("launch", [(128, 1, 128), (256, 2, 2048), (256, 0, 32768), (64, 6, 2048),
-                                    (64, 0, 64)])
+                                    (64, 0, 64), (64, -1, 0), (256, -1, 0)])
 def test_pool_graph_and_launch_shapes(launch):
     n = 6
     frames = _frames(n)
     schedule = [set(range(len(CAMS)))] * 3 + [{0, 2, 4}] * 3
     a = _alone(frames, schedule)
     b, _, _ = _pooled(frames, schedule, graph=True, launch=launch)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+
+
+@pytest.mark.parametrize("launch", [(128, 8, 1024), (64, -1, 0), (256, -1, 0)])
+def test_pool_fp16_launch_shapes(launch):
+    """FP16/BF16 state: the persistent and the flat form (two pixels per
+    lane, a half chunk at each camera's end) equal each camera alone."""
+    n = 5
+    frames = _frames(n)
+    schedule = [set(range(len(CAMS)))] * 3 + [{1, 3, 4}] * 2
+    a = _alone(frames, schedule, precision=G.PREC_F16)
+    b, _, _ = _pooled(frames, schedule, graph=True, launch=launch, precision=G.PREC_F16)
     for key in a:
         assert np.array_equal(a[key], b[key]), key
 
@@ -163,7 +182,7 @@ def test_pool_autotune_leaves_state_unchanged():
             pool.tick()
     before = [pool.planes(c) for c in ids]
     shape = pool.autotune(iters=2)
-    assert shape["threads"] in (64, 128, 256) and shape["tile_pixels"] % shape["threads"] == 0
+    assert _valid_shape(shape)
     after = [pool.planes(c) for c in ids]
     for x, y in zip(before, after):
         assert np.array_equal(x, y)
@@ -172,7 +191,7 @@ def test_pool_autotune_leaves_state_unchanged():
 
 
 def test_pool_online_tuning_changes_nothing_but_speed():
-    """Online tuning runs real ticks under every candidate launch shape (24
+    """Online tuning runs real ticks under every candidate launch shape (27
     of them, one tick each here, graphs requested): the results still equal
     each camera run alone, tuning finishes, and graph use resumes."""
     n = 28
@@ -184,12 +203,12 @@ def test_pool_online_tuning_changes_nothing_but_speed():
         assert np.array_equal(a[key], b[key]), key
     tuning, shape = pool.tuning()
     assert not tuning
-    assert shape["threads"] in (64, 128, 256) and shape["tile_pixels"] % shape["threads"] == 0
+    assert _valid_shape(shape)
     pool.sync()
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_pool_more_cameras_than_one_launch_holds(graph):
+@pytest.mark.parametrize("graph,launch", [(False, None), (True, None), (True, (128, -1, 0))])
+def test_pool_more_cameras_than_one_launch_holds(graph, launch):
     """A tick with more cameras than one launch's parameter block holds (128)
     is split into several launches; every camera still equals its run alone,
     in ticks of changing size (the graph's nodes updated or rebuilt)."""
@@ -213,6 +232,8 @@ def test_pool_more_cameras_than_one_launch_holds(graph):
         g.close()
     pool = G.Pool(max_cams=n_cams)
     pool.use_graph(graph)
+    if launch:
+        pool.set_launch(*launch)
     ids = [pool.admit(H, W, M) for (H, W, M) in shapes]
     pos = [0] * n_cams
     got = {}

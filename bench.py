@@ -775,11 +775,11 @@ def run_pool(args, wl):
                                                 "pooled_over_plain": value / plain_value},
             "latency_ms": {"tick_p50": pct(tick_ms, 50), "tick_p99": pct(tick_ms, 99)},
             "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
-                    "d2h_bytes_per_step": e2e["d2h"],
+                    "d2h_bytes_per_step": e2e["d2h"], "launch": e2e["launch"],
                     "path": "pinned packed tick-sets -> device staging (copy stream) -> "
                             "gmm_pool_submit_many + gmm_pool_tick -> masks to pinned host"},
             "cpu_baseline": cpu,
-            "gpu_launches": K,
+            "gpu_launches": K * pool_launches(cams, shape),
             "clocks": clk,
         }
         if model_flags(args, G):
@@ -790,6 +790,15 @@ def run_pool(args, wl):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def pool_launches(cams, shape):
+    """Kernels per pooled tick: one per 128 cameras; the flat form launches
+    each M group separately."""
+    if shape and shape.get("ctas_per_sm", 0) < 0:
+        ms = [M for (_, _, M, _) in cams]
+        return sum((ms.count(m) + 127) // 128 for m in set(ms))
+    return (len(cams) + 127) // 128
 
 
 def run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, steps, warmup, world):
@@ -842,19 +851,21 @@ def run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, steps, warmup, 
             hmask[k % ring].copy_(dmask[b], non_blocking=True)
             down[b].record(down_s)
 
+    k0 = 0
+    shape = pool.tuning()[1]
     for k in range(warmup):
-        tick(k)
+        tick(k0 + k)
     torch.cuda.synchronize()
     barrier(world, dev)
     t = time.perf_counter()
     for k in range(steps):
-        tick(warmup + k)
+        tick(k0 + warmup + k)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
     barrier(world, dev)
     dt = reduce_max(dt, world, dev)
     px = sum(H * W for (H, W, _, _) in cams)
-    return {"value": world * steps * px / dt / 1e6,
+    return {"value": world * steps * px / dt / 1e6, "launch": shape,
             "h2d": sum(H * W * 5 for (H, W, _, _) in cams),
             "d2h": sum(H * G.mask_words_per_row(W) * 4 for (H, W, _, _) in cams)}
 

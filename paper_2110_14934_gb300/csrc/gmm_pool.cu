@@ -36,10 +36,11 @@ struct PoolCam {
 struct GraphSig {
     int n_launch = -1, threads = 0;
     std::vector<int> blocks; // per launch
+    std::vector<int> m; // per launch: the M its cameras share (flat form), else 0
     bool all_variants = false, flat = false;
     bool operator==(const GraphSig &o) const {
         return n_launch == o.n_launch && threads == o.threads && blocks == o.blocks &&
-               all_variants == o.all_variants && flat == o.flat;
+               m == o.m && all_variants == o.all_variants && flat == o.flat;
     }
 };
 
@@ -52,19 +53,23 @@ struct Shape {
 
 int chunk_pixels(int prec) { return prec == 0 ? 32 : 64; }
 
-// Online tuning: real ticks cycle through candidate launch shapes, each tick
-// timed by an event pair on the pool's stream; when every candidate has run
-// its ticks, the shape with the lowest median tick time is kept.
+// Online tuning: real ticks cycle through candidate launch shapes; a trial
+// tick is timed on the pool's stream from its start to the start of the
+// next tick (the tick period), so a shape is also charged for what its
+// kernel delays in the work queued before the next tick (uploads of the next
+// frames sharing HBM with it, in a pipeline). When every candidate has run
+// its ticks, the shape with the lowest median period is kept.
 struct Trial {
-    int cand;
-    cudaEvent_t a, b;
+    int cand = -1;
+    cudaEvent_t a = nullptr, b = nullptr;
 };
 struct Tuning {
     bool active = false;
     bool saved_graph = false;
     int per_shape = 0, issued = 0;
     std::vector<Shape> cands;
-    std::vector<Trial> pending;
+    Trial open;                 // the last trial tick, until the next tick starts
+    std::vector<Trial> pending; // closed trials not yet read
     std::vector<std::vector<float>> ms;
 };
 
@@ -86,7 +91,8 @@ struct gmm_pool {
     // Tile counters, two sets of kmax (one per launch of a tick): a tick
     // uses set `parity` and its launches zero the other set for the next.
     int *d_counters = nullptr;
-    int kmax = 1, parity = 0;
+    int kmax = 1, parity = 0; // kmax: launches a tick may take
+    std::vector<int> launch_m; // per launch: the M its cameras share (flat form), else 0
     // Launch arguments (kmax per tick) in page-locked memory, two buffers.
     gmmhost::PoolArgs *h_args[kStaging] = {};
     cudaEvent_t ev_staged[kStaging] = {};
@@ -125,8 +131,12 @@ static int blocks_for(gmm_pool *p) {
     return p->sms * per_sm;
 }
 
-// Candidate launch shapes: block sizes; the persistent form at full or half
-// residency with each tile size, and the flat form.
+// Candidate launch shapes: block sizes, full or half residency, tile sizes
+// of the persistent form. (The flat form is left to an explicit choice: it
+// is the faster one for FP32 state with every input already in device
+// memory, but host uploads that run beside it slow it far more than they
+// slow the persistent form, and ticks timed without such uploads cannot
+// tell.)
 static std::vector<Shape> tuning_candidates(const gmm_pool *p) {
     std::vector<Shape> out;
     const int cand_threads[] = {64, 128, 256};
@@ -138,7 +148,6 @@ static std::vector<Shape> tuning_candidates(const gmm_pool *p) {
             if (c >= 1)
                 for (int tp : cand_tiles)
                     out.push_back({t, c, tp});
-        out.push_back({t, -1, chunk_pixels(p->prec)});
     }
     return out;
 }
@@ -174,7 +183,7 @@ static int tuning_poll(gmm_pool *p, bool block) {
     }
     tu.pending.erase(tu.pending.begin(), tu.pending.begin() + (long)k);
     const int total = (int)tu.cands.size() * tu.per_shape;
-    if (tu.issued < total || !tu.pending.empty())
+    if (tu.issued < total || tu.open.a || !tu.pending.empty())
         return GMM_OK;
     int best = 0;
     float best_ms = -1.f;
@@ -199,7 +208,7 @@ static cudaError_t enqueue_body(gmm_pool *p, cudaStream_t s, int b, const GraphS
     cudaError_t e = cudaSuccess;
     for (int li = 0; li < sig.n_launch && e == cudaSuccess; ++li)
         e = gmmhost::launch_pool_tick_impl(&p->h_args[b][li], sig.threads, sig.blocks[li],
-                                           p->prec, sig.all_variants, sig.flat, s);
+                                           p->prec, sig.all_variants, sig.flat, sig.m[li], s);
     return e;
 }
 
@@ -212,9 +221,11 @@ static cudaError_t launch_tick(gmm_pool *p, int b, int n_launch, bool all_varian
     sig.all_variants = all_variants;
     sig.flat = p->ctas_per_sm < 0;
     const int warps = p->threads / 32;
-    for (int li = 0; li < n_launch; ++li) // flat: one warp per chunk
+    for (int li = 0; li < n_launch; ++li) { // flat: one warp per chunk
         sig.blocks.push_back(sig.flat ? (int)((p->h_args[b][li].n_tiles + warps - 1) / warps)
                                       : blocks_for(p));
+        sig.m.push_back(p->launch_m[li]);
+    }
     if (!p->use_graph) {
         cudaError_t e = gmmhost::pool_bank_acquire(p->device, p->stream);
         if (e != cudaSuccess)
@@ -290,8 +301,11 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
     int li = 0, j = 0;
     int64_t tiles = 0;
     bool all_variants = false; // some camera needs the options or the augmented mixture
+    const bool flat = p->ctas_per_sm < 0;
+    int group_m = 0; // flat form: the launch's cameras share M (a kernel per M)
     auto close_launch = [&]() {
         gmmhost::PoolArgs &a = p->h_args[b][li];
+        p->launch_m[li] = group_m;
         a.tile_begin[j] = tiles;
         a.n_jobs = j;
         a.n_tiles = tiles;
@@ -303,39 +317,48 @@ static int pool_tick_impl(gmm_pool *p, bool clear) {
         j = 0;
         tiles = 0;
     };
-    for (PoolCam &c : p->cams) {
-        if (!(c.used && c.submitted))
-            continue;
-        gmmhost::PoolArgs &a = p->h_args[b][li];
-        a.views[j] = make_view(c.cfg, c.L, c.arena, c.rgb, c.depth, c.mask, c.fgr, c.fgd,
-                               c.initialized ? 0 : 1, c.ticks);
-        all_variants = all_variants || gmmhost::view_variant(a.views[j]) != 0;
-        a.tile_begin[j] = tiles;
-        tiles += (c.L.n_pad + unit - 1) / unit;
-        if (++j == gmmhost::kPoolViews)
+    const int groups[3] = {3, 4, 5};
+    for (int gi = 0; gi < (flat ? 3 : 1); ++gi) {
+        group_m = flat ? groups[gi] : 0;
+        for (PoolCam &c : p->cams) {
+            if (!(c.used && c.submitted) || (group_m && c.cfg.M != group_m))
+                continue;
+            gmmhost::PoolArgs &a = p->h_args[b][li];
+            a.views[j] = make_view(c.cfg, c.L, c.arena, c.rgb, c.depth, c.mask, c.fgr, c.fgd,
+                                   c.initialized ? 0 : 1, c.ticks);
+            all_variants = all_variants || gmmhost::view_variant(a.views[j]) != 0;
+            a.tile_begin[j] = tiles;
+            tiles += (c.L.n_pad + unit - 1) / unit;
+            if (++j == gmmhost::kPoolViews)
+                close_launch();
+        }
+        if (j > 0)
             close_launch();
     }
-    if (j > 0)
-        close_launch();
     const int n_launch = li;
     cudaError_t e = cudaSuccess;
+    if (clear && tu.active && tu.open.a) { // this tick's start ends the last trial's period
+        e = cudaEventCreate(&tu.open.b);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(tu.open.b, p->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(&p->sticky, e, "gmm_pool_tick tuning");
+        tu.pending.push_back(tu.open);
+        tu.open = Trial();
+    }
     if (trial) {
         e = cudaEventCreate(&tr.a);
         if (e == cudaSuccess)
-            e = cudaEventCreate(&tr.b);
-        if (e == cudaSuccess)
             e = cudaEventRecord(tr.a, p->stream);
-        if (e != cudaSuccess)
+        if (e != cudaSuccess) {
+            if (tr.a)
+                cudaEventDestroy(tr.a);
             return cuda_fail(&p->sticky, e, "gmm_pool_tick tuning");
+        }
+        tu.open = tr;
+        ++tu.issued;
     }
     e = launch_tick(p, b, n_launch, all_variants);
-    if (e == cudaSuccess && trial) {
-        e = cudaEventRecord(tr.b, p->stream);
-        if (e == cudaSuccess) {
-            tu.pending.push_back(tr);
-            ++tu.issued;
-        }
-    }
     if (e == cudaSuccess)
         e = cudaEventRecord(p->ev_staged[b], p->stream);
     if (e != cudaSuccess)
@@ -379,7 +402,9 @@ gmm_pool_t *gmm_pool_create(size_t budget_bytes, int precision, int max_cams) {
     p->prec = precision;
     p->max_cams = max_cams;
     p->cams.resize((size_t)max_cams);
-    p->kmax = (max_cams + gmmhost::kPoolViews - 1) / gmmhost::kPoolViews;
+    // one launch per kPoolViews cameras, plus one per M group in the flat form
+    p->kmax = (max_cams + gmmhost::kPoolViews - 1) / gmmhost::kPoolViews + 2;
+    p->launch_m.assign((size_t)p->kmax, 0);
     cudaError_t e = cudaGetDevice(&p->device);
     for (int b = 0; b < kStaging && e == cudaSuccess; ++b) {
         e = cudaMallocHost(&p->h_args[b], sizeof(gmmhost::PoolArgs) * (size_t)p->kmax);
@@ -564,6 +589,10 @@ int gmm_pool_autotune_online(gmm_pool_t *p, int ticks_per_shape) {
     if (rc != GMM_OK)
         return rc;
     Tuning &tu = p->tune;
+    if (tu.open.a) { // an unfinished run's last trial: no tick will end it now
+        cudaEventDestroy(tu.open.a);
+        tu.open = Trial();
+    }
     tu.cands = tuning_candidates(p);
     tu.ms.assign(tu.cands.size(), {});
     tu.per_shape = ticks_per_shape;
@@ -743,6 +772,9 @@ int gmm_pool_destroy(gmm_pool_t *p) {
         cudaEventDestroy(tr.b);
     }
     p->tune.pending.clear();
+    if (p->tune.open.a)
+        cudaEventDestroy(p->tune.open.a);
+    p->tune.open = Trial();
     for (PoolCam &c : p->cams)
         if (c.used && c.arena)
             cudaFreeAsync(c.arena, p->stream);

@@ -126,9 +126,11 @@ __device__ __forceinline__ void flat_chunk_v(const CamView &cv, int64_t base) {
     }
 }
 
-// FP32: no residency hint (76 registers, no spills; held to 64 it spills and
-// measured slower). FP16/BF16: 64 registers, as in the other kernels.
-template <int PREC, bool kAll>
+// MM: every camera of the launch has M = MM (the host groups the flat
+// form's launches by M, so each runs a body specialised to its M), or 0
+// (any M, switched per warp). FP32: no residency hint; FP16/BF16: 64
+// registers, as in the other kernels.
+template <int PREC, bool kAll, int MM>
 __global__ void __launch_bounds__(256, PREC == 0 ? 1 : 4) k_pool_flat() {
     const PoolArgs &a = c_pool;
     if (blockIdx.x == 0) // the next tick's counters, as the persistent form does
@@ -147,10 +149,24 @@ __global__ void __launch_bounds__(256, PREC == 0 ? 1 : 4) k_pool_flat() {
     }
     const CamView &cv = a.views[lo];
     const int64_t base = (c - a.tile_begin[lo]) * a.tile_pixels;
+    if (MM != 0) {
+        flat_chunk_v<MM != 0 ? MM : 3, PREC, kAll>(cv, base);
+        return;
+    }
     switch (cv.M) {
     case 3: flat_chunk_v<3, PREC, kAll>(cv, base); break;
     case 4: flat_chunk_v<4, PREC, kAll>(cv, base); break;
     default: flat_chunk_v<5, PREC, kAll>(cv, base); break;
+    }
+}
+
+template <int PREC, bool kAll>
+void launch_flat(int m, int blocks, int threads, cudaStream_t s) {
+    switch (m) {
+    case 3: k_pool_flat<PREC, kAll, 3><<<blocks, threads, 0, s>>>(); break;
+    case 4: k_pool_flat<PREC, kAll, 4><<<blocks, threads, 0, s>>>(); break;
+    case 5: k_pool_flat<PREC, kAll, 5><<<blocks, threads, 0, s>>>(); break;
+    default: k_pool_flat<PREC, kAll, 0><<<blocks, threads, 0, s>>>(); break;
     }
 }
 
@@ -192,20 +208,20 @@ cudaError_t pool_bank_release(int device, cudaStream_t s) {
 }
 
 cudaError_t launch_pool_tick_impl(const PoolArgs *args_host, int threads, int blocks, int prec,
-                                  bool all_variants, bool flat, cudaStream_t s) {
+                                  bool all_variants, bool flat, int m, cudaStream_t s) {
     cudaError_t e = cudaMemcpyToSymbolAsync(c_pool, args_host, sizeof(PoolArgs), 0,
                                             cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess)
         return e;
     if (flat) {
         if (prec == 0 && !all_variants)
-            k_pool_flat<0, false><<<blocks, threads, 0, s>>>();
+            launch_flat<0, false>(m, blocks, threads, s);
         else if (prec == 0)
-            k_pool_flat<0, true><<<blocks, threads, 0, s>>>();
+            launch_flat<0, true>(m, blocks, threads, s);
         else if (!all_variants)
-            k_pool_flat<1, false><<<blocks, threads, 0, s>>>();
+            launch_flat<1, false>(m, blocks, threads, s);
         else
-            k_pool_flat<1, true><<<blocks, threads, 0, s>>>();
+            launch_flat<1, true>(m, blocks, threads, s);
     } else if (prec == 0 && !all_variants)
         k_pool_tick<0, false><<<blocks, threads, 0, s>>>();
     else if (prec == 0)

@@ -24,7 +24,7 @@ from parity import FREE_RUN_EPS, state_mismatch, words
 pytestmark = pytest.mark.gpu
 
 PRM = dict(alpha=0.01, match_k=2.5, bg_T=0.7, init_var=225.0, init_w=0.05)
-T = 32          # ticks: the first 27 run the online tuner's candidate shapes
+T = 32          # ticks: the first 24 run the online tuner's candidate shapes
 BAND = 2        # rows per camera checked against the oracle
 
 

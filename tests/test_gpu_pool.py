@@ -191,7 +191,7 @@ def test_pool_autotune_leaves_state_unchanged():
 
 
 def test_pool_online_tuning_changes_nothing_but_speed():
-    """Online tuning runs real ticks under every candidate launch shape (27
+    """Online tuning runs real ticks under every candidate launch shape (24
     of them, one tick each here, graphs requested): the results still equal
     each camera run alone, tuning finishes, and graph use resumes."""
     n = 28

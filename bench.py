@@ -539,8 +539,8 @@ def run_gmm(args, wl):
     peak, peak_src = measured_hbm_peak()
     # the captures are of the default kernel instance on the 1920x1080 M=5 workload
     traffic = (recorded_traffic("tick", prec, H * W * bpp)
-               if args.workload == "c1" and args.kernel == "direct" and args.variant == 0
-               and not model_flags(args, G) else None)
+               if args.workload == "c1" and not args.frame_size and args.kernel == "direct"
+               and args.variant == 0 and not model_flags(args, G) else None)
 
     # end to end through the host-memory C-ABI path (pipelined, Fig. 4(a))
     e2e = run_e2e(G, torch, g_args=(H, W, M, prec), frames=(rgb_d, dep_d), dev=dev,
@@ -1262,6 +1262,8 @@ def main(argv=None):
     ap.add_argument("--pool-launch", default="",
                     help="pooled workloads: THREADS,CTAS_PER_SM,TILE_PIXELS instead of tuning "
                          "(CTAS_PER_SM -1: the flat form)")
+    ap.add_argument("--frame-size", default="",
+                    help="single-camera workloads: WIDTHxHEIGHT instead of the workload's")
     ap.add_argument("--frames", type=int, default=0,
                     help="resident frames to cycle through (0: the workload's sequence length)")
     ap.add_argument("--stochastic-weights", action="store_true",
@@ -1282,6 +1284,10 @@ def main(argv=None):
     if args.precision != "default":
         wl["prec"] = 0 if args.precision == "f32" else 1
         wl["name"] += f" [state overridden: {args.precision}]"
+    if args.frame_size and not (wl.get("pool") or wl.get("serve")):
+        W_, H_ = (int(v) for v in args.frame_size.lower().split("x"))
+        wl["H"], wl["W"] = H_, W_
+        wl["name"] += f" [frame {W_}x{H_}]"
     if args.cams_per_res and (wl.get("pool") or wl.get("serve")):
         wl["cams_per_res"] = args.cams_per_res
         wl["name"] += f" [{args.cams_per_res} cameras per resolution]"

@@ -20,8 +20,20 @@ namespace {
 // ------------------------------------------------------------ single camera
 // FP32 state: one thread per padded pixel (n_pad is a multiple of 32: whole
 // warps leave).
+// Programmatic dependent launch between consecutive ticks on a stream: a
+// tick waits for the kernel before it to complete (and its writes to be
+// visible) before it reads anything, then lets the next tick be scheduled,
+// so the next tick's CTAs take the SMs this tick's last CTAs leave idle
+// instead of waiting for a full launch. (Both are no-ops when the kernel was
+// not launched as a dependent.)
+__device__ __forceinline__ void tick_prologue() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <int M, int PREC, int V>
 __device__ __forceinline__ void tick_body(const CamView &cv) {
+    tick_prologue();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= cv.n_pad)
         return;
@@ -35,6 +47,7 @@ __device__ __forceinline__ void tick_body(const CamView &cv) {
 // is skipped by the whole warp.
 template <int M, int PREC, int V>
 __device__ __forceinline__ void tick_body2(const CamView &cv) {
+    tick_prologue();
     const int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 64;
     if (base >= cv.n_pad)
         return;
@@ -65,15 +78,22 @@ __global__ void __launch_bounds__(256, 4) k_tick_f16(const CamView cv) { tick_bo
 
 template <int M, int PREC, int V>
 cudaError_t launch_tick_v(const CamView &cv, int threads, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (PREC == 0) {
-        const int64_t blocks = (cv.n_pad + threads - 1) / threads;
-        k_tick_f32<M, V><<<(unsigned)blocks, threads, 0, s>>>(cv);
-    } else {
-        const int64_t chunks = (cv.n_pad + 63) / 64; // one per warp
-        const int warps = threads / 32;
-        k_tick_f16<M, V><<<(unsigned)((chunks + warps - 1) / warps), threads, 0, s>>>(cv);
+        cfg.gridDim = dim3((unsigned)((cv.n_pad + threads - 1) / threads));
+        return cudaLaunchKernelEx(&cfg, k_tick_f32<M, V>, cv);
     }
-    return cudaGetLastError();
+    const int64_t chunks = (cv.n_pad + 63) / 64; // one per warp
+    const int warps = threads / 32;
+    cfg.gridDim = dim3((unsigned)((chunks + warps - 1) / warps));
+    return cudaLaunchKernelEx(&cfg, k_tick_f16<M, V>, cv);
 }
 
 template <int M, int PREC>

@@ -26,14 +26,14 @@ namespace {
 // so the next tick's CTAs take the SMs this tick's last CTAs leave idle
 // instead of waiting for a full launch. (Both are no-ops when the kernel was
 // not launched as a dependent.)
-__device__ __forceinline__ void tick_prologue() {
+__device__ __forceinline__ void dependent_launch_prologue() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 template <int M, int PREC, int V>
 __device__ __forceinline__ void tick_body(const CamView &cv) {
-    tick_prologue();
+    dependent_launch_prologue();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= cv.n_pad)
         return;
@@ -47,7 +47,7 @@ __device__ __forceinline__ void tick_body(const CamView &cv) {
 // is skipped by the whole warp.
 template <int M, int PREC, int V>
 __device__ __forceinline__ void tick_body2(const CamView &cv) {
-    tick_prologue();
+    dependent_launch_prologue();
     const int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 64;
     if (base >= cv.n_pad)
         return;
@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(kMR * kMW) k_morph_open3(const uint32_t *in, u
     __shared__ uint32_t s_h[kMR + 4][kMW + 2];   // horizontal erosion, words w0-1..
     __shared__ uint32_t s_e[kMR + 2][kMW + 2];   // erosion, rows r0-1.., words w0-1..
     __shared__ uint32_t s_hd[kMR + 2][kMW];      // horizontal dilation, words w0..
+    dependent_launch_prologue(); // the mask it reads is complete; the next tick may be scheduled
     const int r0 = blockIdx.y * kMR, w0 = blockIdx.x * kMW;
     const int tid = threadIdx.y * kMW + threadIdx.x, nt = kMR * kMW;
 
@@ -282,9 +283,17 @@ cudaError_t launch_fuse(const uint32_t *fg_rgb, const uint32_t *fg_d, uint8_t *f
 
 cudaError_t launch_morph_open3(const uint32_t *in, uint32_t *out, int H, int W, cudaStream_t s) {
     const int wpr = (W + 31) / 32;
-    dim3 grid((unsigned)((wpr + kMW - 1) / kMW), (unsigned)((H + kMR - 1) / kMR));
-    k_morph_open3<<<grid, dim3(kMW, kMR), 0, s>>>(in, out, H, W, wpr);
-    return cudaGetLastError();
+    // a programmatic dependent of the kernel before it, like the ticks
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3((unsigned)((wpr + kMW - 1) / kMW), (unsigned)((H + kMR - 1) / kMR));
+    cfg.blockDim = dim3(kMW, kMR);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_morph_open3, in, out, H, W, wpr);
 }
 
 cudaError_t launch_pack(const uint8_t *in, uint32_t *out, int H, int W, cudaStream_t s) {

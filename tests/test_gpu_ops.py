@@ -78,6 +78,42 @@ def test_handle_with_morph_open():
         assert np.array_equal(G.unpack_mask(words(b), H, W), ref)
 
 
+@pytest.mark.parametrize("prec,morph,reuse", [(G.PREC_F32, False, False), (G.PREC_F16, False, False),
+                                              (G.PREC_F32, True, False), (G.PREC_F32, False, True),
+                                              (G.PREC_F16, True, True)])
+def test_back_to_back_ticks_equal_synchronised_ticks(prec, morph, reuse):
+    """Consecutive ticks (and openings) are launched as programmatic
+    dependents of the kernel before them. Queued back to back with no host
+    synchronisation (directly one after another, or with each frame copied
+    into one reused input buffer, and that buffer cleared after the tick, by
+    ordinary stream work in between), the masks and the final state equal a
+    run that synchronises the device after every tick."""
+    import torch
+    H, W, M, n = 96, 160, 5, 24
+    rgb, depth, _ = scene_frames(31, H, W, 1, 0, n)
+    frames = [to_dev(rgb[t], depth[t]) for t in range(n)]
+    ref_g = G.GMM(H, W, M, precision=prec, morph_open=morph)
+    ref = []
+    for t in range(n):
+        ref.append(words(ref_g.apply(*frames[t])).copy())
+        torch.cuda.synchronize()
+    g = G.GMM(H, W, M, precision=prec, morph_open=morph)
+    r_buf, d_buf = torch.empty_like(frames[0][0]), torch.empty_like(frames[0][1])
+    outs = [g.new_mask() for _ in range(n)]
+    for t in range(n):
+        if reuse:
+            r_buf.copy_(frames[t][0])
+            d_buf.copy_(frames[t][1])
+            g.apply(r_buf, d_buf, outs[t])
+            r_buf.zero_()  # may only land after this tick read the frame
+        else:
+            g.apply(*frames[t], outs[t])
+    torch.cuda.synchronize()
+    for t in range(n):
+        assert np.array_equal(words(outs[t]), ref[t]), t
+    assert np.array_equal(g.planes(), ref_g.planes())
+
+
 def test_host_path_and_pipeline_match_device_path():
     import torch
     H, W, M = 50, 70, 4

@@ -203,7 +203,11 @@ int gmm_set_kernel(gmm_t *h, int kind, int variant, int ctas_per_sm);
  * mask_out: device, receives the fused foreground (bit-packed, see top), or
  * its 3x3 opening when the handle was created with morph_open = 1.
  * Asynchronous on the handle's stream. The first call after create (or
- * gmm_reset) initialises the models from this frame. */
+ * gmm_reset) initialises the models from this frame. The direct tick (and
+ * the opening) is launched as a programmatic dependent of the kernel before
+ * it on the stream: it may be scheduled while that kernel's last CTAs run,
+ * but reads nothing until that kernel has completed and its writes are
+ * visible, so stream order holds as for any launch. */
 int gmm_apply(gmm_t *h, const uint8_t *rgb8, const uint16_t *depth16,
               uint32_t *mask_out);
 

@@ -579,6 +579,11 @@ def run_gmm(args, wl):
             "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
                     "d2h_bytes_per_step": e2e["d2h"], "path": "gmm_pipe_submit/gmm_pipe_wait, "
                     "pinned host frames, 3 frames in flight"},
+            "e2e_zero_copy": {"value": e2e["zero_copy"], "unit": UNIT,
+                              "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                              "path": "gmm_apply on the same page-locked host frames and masks: "
+                                      "the kernel reads the frame and writes the mask over the "
+                                      "host link, timed to the last mask in host memory"},
             "cpu_baseline": cpu,
             "gpu_launches": K * (2 if args.morph else 1),
             "clocks": clk if clocks else None,
@@ -1236,8 +1241,27 @@ def run_e2e(G, torch, g_args, frames, dev, steps, warmup, world, kernel, morph=F
         lat.append((time.perf_counter() - t0) * 1e3)
     lat.sort()
     g.close()
+    # zero-copy: gmm_apply on the same page-locked host frames and masks, the
+    # kernel reading the frame and writing the mask over the host link
+    zg = G.GMM(H, W, M, precision=prec, device=dev, morph_open=morph, **PARAMS)
+    zg.set_kernel(*kernel)
+    stream = torch.cuda.current_stream(dev)
+    for k in range(warmup):
+        zg.apply(rgb_h[k % n_host], dep_h[k % n_host], masks[k % ring], stream=stream)
+    torch.cuda.synchronize()
+    barrier(world, dev)
+    t = time.perf_counter()
+    for k in range(steps):
+        zg.apply(rgb_h[(warmup + k) % n_host], dep_h[(warmup + k) % n_host],
+                 masks[(warmup + k) % ring], stream=stream)
+    torch.cuda.synchronize()
+    dz = time.perf_counter() - t
+    barrier(world, dev)
+    dz = reduce_max(dz, world, dev)
+    zg.close()
     return {"value": world * steps * H * W / dt / 1e6, "h2d": H * W * 5,
-            "d2h": H * G.mask_words_per_row(W) * 4, "lat_p50": pct(lat, 50), "lat_p99": pct(lat, 99)}
+            "d2h": H * G.mask_words_per_row(W) * 4, "lat_p50": pct(lat, 50), "lat_p99": pct(lat, 99),
+            "zero_copy": world * steps * H * W / dz / 1e6}
 
 
 def main(argv=None):

@@ -201,7 +201,11 @@ int gmm_set_kernel(gmm_t *h, int kind, int variant, int ctas_per_sm);
 /* One tick (§III.A-C, §IV): both mixtures and the List-1 fusion for one
  * RGB-D frame, in one fused kernel. rgb8, depth16: device, read-only.
  * mask_out: device, receives the fused foreground (bit-packed, see top), or
- * its 3x3 opening when the handle was created with morph_open = 1.
+ * its 3x3 opening when the handle was created with morph_open = 1. Any of
+ * the three may instead be page-locked host memory mapped into the device's
+ * address space (cudaHostAlloc or cudaHostRegister under unified
+ * addressing): the kernel then reads the frame or writes the mask there
+ * directly over the host link, with no separate copy (zero-copy).
  * Asynchronous on the handle's stream. The first call after create (or
  * gmm_reset) initialises the models from this frame. The direct tick (and
  * the opening) is launched as a programmatic dependent of the kernel before

@@ -114,6 +114,26 @@ def test_back_to_back_ticks_equal_synchronised_ticks(prec, morph, reuse):
     assert np.array_equal(g.planes(), ref_g.planes())
 
 
+@pytest.mark.parametrize("prec", [G.PREC_F32, G.PREC_F16])
+def test_zero_copy_host_buffers_match_device_path(prec):
+    """gmm_apply on page-locked host frames and a page-locked host mask (the
+    kernel reads and writes them over the host link) equals the device path."""
+    import torch
+    H, W, M = 70, 100, 5
+    rgb, depth, _ = scene_frames(41, H, W, 1, 0, 6)
+    dev = G.GMM(H, W, M, precision=prec)
+    zc = G.GMM(H, W, M, precision=prec)
+    for t in range(6):
+        ref = words(dev.apply(*to_dev(rgb[t], depth[t]))).copy()
+        r = torch.from_numpy(rgb[t].copy()).pin_memory()
+        d = torch.from_numpy(depth[t].view(np.int16).copy()).pin_memory()
+        m = torch.zeros((H, G.mask_words_per_row(W)), dtype=torch.int32).pin_memory()
+        zc.apply(r, d, m)
+        torch.cuda.synchronize()
+        assert np.array_equal(m.numpy().view(np.uint32), ref), t
+    assert np.array_equal(zc.planes(), dev.planes())
+
+
 def test_host_path_and_pipeline_match_device_path():
     import torch
     H, W, M = 50, 70, 4

@@ -91,10 +91,15 @@ def bytes_per_pixel(M: int, prec: int) -> float:
 
 
 def kernel_source_hash(sources=None) -> str:
+    """Hash of the kernel sources' code: comments removed and whitespace
+    collapsed, so only a change of the code itself voids a recorded capture."""
     h = hashlib.sha256()
     for f in sources or KERNEL_SOURCES:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

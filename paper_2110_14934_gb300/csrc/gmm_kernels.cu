@@ -18,8 +18,6 @@ using gmmhost::PoolArgs;
 namespace {
 
 // ------------------------------------------------------------ single camera
-// FP32 state: one thread per padded pixel (n_pad is a multiple of 32: whole
-// warps leave).
 // Programmatic dependent launch between consecutive ticks on a stream: a
 // tick waits for the kernel before it to complete (and its writes to be
 // visible) before it reads anything, then lets the next tick be scheduled,
@@ -31,6 +29,8 @@ __device__ __forceinline__ void dependent_launch_prologue() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// FP32 state: one thread per padded pixel (n_pad is a multiple of 32: whole
+// warps leave).
 template <int M, int PREC, int V>
 __device__ __forceinline__ void tick_body(const CamView &cv) {
     dependent_launch_prologue();

@@ -1,7 +1,6 @@
 """Host logic of bench.py that decides what a bench line reports: the
 recorded-traffic lookup and its source hash, the serving schedule, the
 latency split from the engine's traces, and the pooled launch count. No GPU."""
-import os
 
 import numpy as np
 

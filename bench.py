@@ -1185,7 +1185,8 @@ def run_serving(args, wl):
                         "sessions_admitted": st["admitted"], "admissions_rejected": st["rejected"],
                         "ticks": st["ticks"], "mean_frames_per_tick": st["completed"] / max(st["ticks"], 1),
                         "driver_lag_ms_p99": fnum(pct(lag, 99)),
-                        "driver_lag_ms_max": fnum(lag[-1]) if lag else None, "release_errors": len(rel_err),
+                        "driver_lag_ms_max": fnum(lag[-1]) if lag else None,
+                        "engine_gap_ms_max": st.get("max_engine_gap_ms"), "release_errors": len(rel_err),
                         "admit_ms_p50": fnum(pct(admit_ms, 50)), "admit_ms_max":
                             fnum(admit_ms[-1]) if admit_ms else None,
                         "budget_gb": wl["budget_gb"]},

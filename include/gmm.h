@@ -460,6 +460,11 @@ typedef struct gmm_server_stats {
     long long pixels;                     /* pixels of completed frames */
     int live_cams;
     size_t budget_bytes, used_bytes;      /* state + staging of admitted cameras */
+    double max_engine_gap_ms;             /* longest time between two passes of the
+                                             engine's loop (a pass waits at most
+                                             0.2 ms for work; a longer gap means the
+                                             thread was blocked, in a CUDA call or a
+                                             lock, or not scheduled) */
 } gmm_server_stats;
 
 /* budget_bytes caps the device memory of admitted cameras (state plus the
@@ -495,9 +500,9 @@ int gmm_server_done(gmm_server_t *s, long long ticket);
  * bound ran out. */
 int gmm_server_wait(gmm_server_t *s, long long ticket, int timeout_ms);
 
-/* Counters, and the recorded per-frame latencies in milliseconds (arrival
- * to mask in host memory, in completion order; copies up to n, returns how
- * many were recorded in total). */
+/* Counters, and the per-frame latencies in milliseconds (arrival to mask in
+ * host memory, in completion order; the most recent 1,048,576 frames are
+ * kept): copies up to n, returns how many are kept. */
 int gmm_server_stats_get(gmm_server_t *s, gmm_server_stats *out);
 size_t gmm_server_latencies(gmm_server_t *s, float *ms_out, size_t n);
 
@@ -513,8 +518,9 @@ typedef struct gmm_server_trace {
     double t_arrival, t_pushed, t_batched, t_submitted, t_done;
 } gmm_server_trace;
 
-/* Copies up to n records, in completion order (the order of
- * gmm_server_latencies), into out; returns how many were recorded. */
+/* Copies up to n records, in completion order (the records of
+ * gmm_server_latencies, the same frames), into out; returns how many are
+ * kept. */
 size_t gmm_server_traces(gmm_server_t *s, gmm_server_trace *out, size_t n);
 
 /* Seconds on the engine's monotonic clock (the clock of t_arrival). */

@@ -57,7 +57,7 @@ class ServerStats(ctypes.Structure):
                 ("rejected", ctypes.c_longlong), ("released", ctypes.c_longlong),
                 ("ticks", ctypes.c_longlong), ("pixels", ctypes.c_longlong),
                 ("live_cams", ctypes.c_int), ("budget_bytes", ctypes.c_size_t),
-                ("used_bytes", ctypes.c_size_t)]
+                ("used_bytes", ctypes.c_size_t), ("max_engine_gap_ms", ctypes.c_double)]
 
 
 class ServerTrace(ctypes.Structure):

@@ -52,6 +52,8 @@ struct SrvCam {
     bool in_flight = false;
 };
 
+constexpr size_t kMaxRecords = size_t(1) << 20; // latencies and traces kept
+
 struct TickRec {
     cudaEvent_t done = nullptr;
     double t_submitted = 0.0; // copies and launch queued
@@ -73,10 +75,14 @@ struct gmm_server {
     std::condition_variable cv_work, cv_done;
     std::thread engine;
     std::atomic<bool> stop{false}, abort_now{false};
+    std::atomic<double> max_gap_ms{0.0}; // longest gap between engine loop passes
     // Per-ticket and per-frame records grow in chunks (no reallocation
-    // copies a growing array while the lock that pushes need is held).
-    std::deque<signed char> done; // per ticket: 0 pending, 1 done, -1 failed
-    long long next_ticket = 0;
+    // copies a growing array while the lock that pushes need is held) and
+    // stay bounded on a long-running server: ticket states before the first
+    // one not yet done are dropped (done_base counts them), and only the
+    // most recent kMaxRecords latencies and traces are kept.
+    std::deque<signed char> done; // tickets done_base..: 0 pending, 1 done, -1 failed
+    long long done_base = 0, next_ticket = 0;
     std::deque<float> lat_ms;
     std::deque<gmm_server_trace> traces; // parallel to lat_ms
     gmm_server_stats st{};
@@ -85,6 +91,11 @@ struct gmm_server {
     std::deque<TickRec> inflight;
     std::vector<cudaEvent_t> ev_pool;
 };
+
+// State of a ticket (caller holds s->mu): tickets before done_base are done.
+static int ticket_state(const gmm_server *s, long long ticket) {
+    return ticket < s->done_base ? 1 : s->done[(size_t)(ticket - s->done_base)];
+}
 
 static void finish_tick(gmm_server *s, TickRec &t, bool ok) {
     const double tnow = clock_s();
@@ -98,12 +109,20 @@ static void finish_tick(gmm_server *s, TickRec &t, bool ok) {
                 s->traces.push_back(gmm_server_trace{j.second.ticket, j.first, (int)t.jobs.size(),
                                                      j.second.t_arrival, j.second.t_pushed,
                                                      j.second.t_batched, t.t_submitted, tnow});
-                s->done[(size_t)j.second.ticket] = 1;
+                s->done[(size_t)(j.second.ticket - s->done_base)] = 1;
                 s->st.completed += 1;
                 s->st.pixels += (long long)c.cfg.H * c.cfg.W;
             } else {
-                s->done[(size_t)j.second.ticket] = -1;
+                s->done[(size_t)(j.second.ticket - s->done_base)] = -1;
             }
+        }
+        while (!s->done.empty() && s->done.front() == 1) {
+            s->done.pop_front();
+            ++s->done_base;
+        }
+        while (s->lat_ms.size() > kMaxRecords) {
+            s->lat_ms.pop_front();
+            s->traces.pop_front();
         }
     }
     s->ev_pool.push_back(t.done);
@@ -177,7 +196,12 @@ static cudaError_t enqueue_tick(gmm_server *s, TickRec &t) {
 
 static void engine_main(gmm_server *s) {
     cudaSetDevice(s->device);
+    double last_pass = clock_s();
     for (;;) {
+        const double now = clock_s();
+        if ((now - last_pass) * 1e3 > s->max_gap_ms.load(std::memory_order_relaxed))
+            s->max_gap_ms.store((now - last_pass) * 1e3, std::memory_order_relaxed);
+        last_pass = now;
         harvest(s, false);
         TickRec t;
         bool quit = false;
@@ -428,7 +452,7 @@ int gmm_server_done(gmm_server_t *s, long long ticket) {
     std::lock_guard<std::mutex> lk(s->mu);
     if (ticket < 0 || ticket >= s->next_ticket)
         return fail(GMM_EINVAL, "gmm_server_done: unknown ticket");
-    const int d = s->done[(size_t)ticket];
+    const int d = ticket_state(s, ticket);
     return d < 0 ? fail(GMM_ECUDA, "gmm_server_done: the frame's tick failed") : d;
 }
 
@@ -438,12 +462,12 @@ int gmm_server_wait(gmm_server_t *s, long long ticket, int timeout_ms) {
     std::unique_lock<std::mutex> lk(s->mu);
     if (ticket < 0 || ticket >= s->next_ticket)
         return fail(GMM_EINVAL, "gmm_server_wait: unknown ticket");
-    auto ready = [&] { return s->done[(size_t)ticket] != 0; };
+    auto ready = [&] { return ticket_state(s, ticket) != 0; };
     if (timeout_ms < 0)
         s->cv_done.wait(lk, ready);
     else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
         return fail(GMM_ETIMEOUT, "gmm_server_wait: timed out");
-    return s->done[(size_t)ticket] > 0 ? GMM_OK
+    return ticket_state(s, ticket) > 0 ? GMM_OK
                                        : fail(GMM_ECUDA, "gmm_server_wait: the frame's tick failed");
 }
 
@@ -452,6 +476,7 @@ int gmm_server_stats_get(gmm_server_t *s, gmm_server_stats *out) {
         return fail(GMM_EINVAL, "gmm_server_stats_get: null argument");
     std::lock_guard<std::mutex> lk(s->mu);
     *out = s->st;
+    out->max_engine_gap_ms = s->max_gap_ms.load(std::memory_order_relaxed);
     return GMM_OK;
 }
 

@@ -156,3 +156,16 @@ def test_server_trace_struct_matches_header():
     assert ctypes.sizeof(G.ServerTrace) == 56
     L = G.load_library()
     assert L.gmm_server_traces(None, None, 0) == 0
+
+
+def test_server_stats_struct_matches_header():
+    """The ctypes mirror of gmm_server_stats lists the header's fields in
+    order, with C's layout."""
+    text = open(os.path.join(ROOT, "include", "gmm.h")).read()
+    body = text[text.index("typedef struct gmm_server_stats {"):text.index("} gmm_server_stats;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in re.findall(r"^\s*(?:long long|int|size_t|double)\s+([^;]+);", body, re.M):
+        names += [n.strip() for n in decl.split(",")]
+    assert names == [f[0] for f in G.ServerStats._fields_]
+    assert ctypes.sizeof(G.ServerStats) == 8 * 8 + 8 + 8 * 2 + 8

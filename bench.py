@@ -958,6 +958,16 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
     import numpy as np
     srv = G.Server(budget_bytes=budget_bytes, precision=wl["prec"], max_cams=len(cams),
                    queue_depth=queue_depth)
+    # device memory for every camera's state and staging mapped before the
+    # clock starts (up to the budget), so no admission maps new memory
+
+    def al(x):
+        return (x + 255) // 256 * 256
+    state_all = sum(G.state_bytes(H, W, M, wl["prec"]) for (H, W, M, _) in cams)
+    stage_all = sum(al(H * W * 3) + al(H * W * 2) + al(H * G.mask_words_per_row(W) * 4)
+                    for (H, W, _, _) in cams)
+    cap = budget_bytes if budget_bytes else state_all + stage_all
+    srv.reserve(min(state_all, cap), min(stage_all, max(cap - min(state_all, cap), 0)))
     events = serving_schedule(len(cams), duration, wl["fps"], wl["session_frames"] / wl["fps"],
                               wl["live_fraction"], seed, genlocked)
     n_slot = queue_depth + 4

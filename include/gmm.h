@@ -437,6 +437,13 @@ int gmm_pool_state_get(const gmm_pool_t *p, int cam, int plane, int component,
 /* Summed state bytes of admitted cameras, and the budget. */
 size_t gmm_pool_state_used(const gmm_pool_t *p);
 
+/* Map `bytes` of device memory into the pool's allocator up front (at most
+ * the budget): allocated and freed once, it stays reserved, so later
+ * admissions take their state without mapping new device memory (mapping
+ * can stall every thread of the process). Synchronous; counts nothing
+ * against the budget. */
+int gmm_pool_reserve(gmm_pool_t *p, size_t bytes);
+
 int gmm_pool_sync(gmm_pool_t *p);
 int gmm_pool_destroy(gmm_pool_t *p);
 
@@ -478,6 +485,10 @@ gmm_server_t *gmm_server_create(size_t budget_bytes, int precision, int max_cams
  * or GMM_EBUDGET when its memory would exceed the budget (the admission is
  * rejected and counted), or another negative status. */
 int gmm_server_admit(gmm_server_t *s, const gmm_config *cfg);
+
+/* As gmm_pool_reserve for the server: state_bytes for camera state,
+ * staging_bytes for the per-camera upload and mask buffers. */
+int gmm_server_reserve(gmm_server_t *s, size_t state_bytes, size_t staging_bytes);
 
 /* End a camera's session: waits (up to timeout_ms; < 0 = no bound) until
  * its queued frames are done, then frees its slot and memory. */

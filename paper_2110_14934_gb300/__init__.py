@@ -137,6 +137,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_server_wait": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_int]),
         "gmm_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
         "gmm_server_latencies": (ctypes.c_size_t, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+        "gmm_server_reserve": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.c_size_t]),
+        "gmm_pool_reserve": (ctypes.c_int, [_vp, ctypes.c_size_t]),
         "gmm_server_traces": (ctypes.c_size_t, [_vp, ctypes.POINTER(ServerTrace), ctypes.c_size_t]),
         "gmm_server_now": (ctypes.c_double, []),
         "gmm_server_destroy": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -385,6 +387,10 @@ class Pool:
     def set_stream(self, stream) -> None:
         _check(load_library().gmm_pool_set_stream(self._p, _stream_ptr(stream, self.device)))
 
+    def reserve(self, nbytes: int) -> None:
+        """Map nbytes of device memory for camera state up front."""
+        _check(load_library().gmm_pool_reserve(self._p, int(nbytes)))
+
     def set_launch(self, threads=0, ctas_per_sm=0, tile_pixels=0) -> None:
         """Launch shape: block size; persistent CTAs per SM and tile size, or
         ctas_per_sm=-1 for the flat form (one chunk per warp). 0 keeps."""
@@ -473,6 +479,10 @@ class Server:
         cam = _check(L.gmm_server_admit(self._s, ctypes.byref(cfg)))
         self.cams[cam] = (int(H), int(W), int(M))
         return cam
+
+    def reserve(self, state_bytes: int, staging_bytes: int) -> None:
+        """Map device memory for camera state and staging up front."""
+        _check(load_library().gmm_server_reserve(self._s, int(state_bytes), int(staging_bytes)))
 
     def release(self, cam: int, timeout_ms: int = -1) -> None:
         _check(load_library().gmm_server_release(self._s, cam, timeout_ms))

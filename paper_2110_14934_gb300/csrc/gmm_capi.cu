@@ -335,6 +335,17 @@ cudaError_t make_retaining_pool(int device, uint64_t keep_bytes, cudaMemPool_t *
     return e;
 }
 
+cudaError_t reserve_in_pool(cudaMemPool_t pool, size_t bytes, cudaStream_t s) {
+    if (bytes == 0)
+        return cudaSuccess;
+    void *p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+    if (e == cudaSuccess)
+        e = cudaFreeAsync(p, s);
+    const cudaError_t es = cudaStreamSynchronize(s);
+    return e != cudaSuccess ? e : es;
+}
+
 int wait_event(cudaEvent_t ev, int timeout_ms, cudaError_t *sticky, const char *what) {
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {

@@ -61,5 +61,9 @@ int wait_event(cudaEvent_t ev, int timeout_ms, cudaError_t *sticky, const char *
 // freed memory mapped (the default pool returns it to the system at the next
 // synchronisation, so cameras that join later would pay for mapping again).
 cudaError_t make_retaining_pool(int device, uint64_t keep_bytes, cudaMemPool_t *out);
+// Allocates `bytes` from the pool on stream s and frees it again, then waits:
+// the pool keeps that memory mapped (up to its release threshold), so later
+// allocations of up to that much take it without mapping new pages.
+cudaError_t reserve_in_pool(cudaMemPool_t pool, size_t bytes, cudaStream_t s);
 
 } // namespace gmmlib

@@ -473,6 +473,21 @@ int gmm_pool_admit(gmm_pool_t *p, const gmm_config *cfg) {
     return slot;
 }
 
+int gmm_pool_reserve(gmm_pool_t *p, size_t bytes) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_reserve: null pool");
+    if (p->budget && bytes > p->budget)
+        bytes = p->budget;
+    DeviceGuard g(p->device);
+    const cudaError_t e = reserve_in_pool(p->mempool, bytes, p->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? GMM_ENOMEM : GMM_ECUDA,
+                    std::string("gmm_pool_reserve: ") + cudaGetErrorString(e));
+    }
+    return GMM_OK;
+}
+
 int gmm_pool_release(gmm_pool_t *p, int cam) {
     if (!valid_cam(p, cam))
         return fail(GMM_EINVAL, "gmm_pool_release: unknown camera");

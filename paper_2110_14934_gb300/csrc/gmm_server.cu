@@ -389,6 +389,23 @@ int gmm_server_admit(gmm_server_t *s, const gmm_config *cfg) {
     return slot;
 }
 
+int gmm_server_reserve(gmm_server_t *s, size_t state_bytes, size_t staging_bytes) {
+    if (!s)
+        return fail(GMM_EINVAL, "gmm_server_reserve: null server");
+    DeviceGuard g(s->device);
+    std::lock_guard<std::mutex> plk(s->pool_mu);
+    const int rc = gmm_pool_reserve(s->pool, state_bytes);
+    if (rc != GMM_OK)
+        return rc;
+    const cudaError_t e = reserve_in_pool(s->mempool, staging_bytes, s->s_comp);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? GMM_ENOMEM : GMM_ECUDA,
+                    std::string("gmm_server_reserve: ") + cudaGetErrorString(e));
+    }
+    return GMM_OK;
+}
+
 int gmm_server_release(gmm_server_t *s, int cam, int timeout_ms) {
     if (!s)
         return fail(GMM_EINVAL, "gmm_server_release: null server");

@@ -440,8 +440,9 @@ size_t gmm_pool_state_used(const gmm_pool_t *p);
 /* Map `bytes` of device memory into the pool's allocator up front (at most
  * the budget): allocated and freed once, it stays reserved, so later
  * admissions take their state without mapping new device memory (mapping
- * can stall every thread of the process). Synchronous; counts nothing
- * against the budget. */
+ * can stall every thread of the process). Synchronous on the pool's stream;
+ * counts nothing against the budget. GMM_ENOMEM if the device cannot
+ * supply it, GMM_ECUDA on another CUDA failure (not sticky). */
 int gmm_pool_reserve(gmm_pool_t *p, size_t bytes);
 
 int gmm_pool_sync(gmm_pool_t *p);
@@ -487,7 +488,9 @@ gmm_server_t *gmm_server_create(size_t budget_bytes, int precision, int max_cams
 int gmm_server_admit(gmm_server_t *s, const gmm_config *cfg);
 
 /* As gmm_pool_reserve for the server: state_bytes for camera state,
- * staging_bytes for the per-camera upload and mask buffers. */
+ * staging_bytes for the per-camera upload and mask buffers; same statuses.
+ * May be called from any thread; it waits for the engine's current
+ * launch to be queued, not for the device. */
 int gmm_server_reserve(gmm_server_t *s, size_t state_bytes, size_t staging_bytes);
 
 /* End a camera's session: waits (up to timeout_ms; < 0 = no bound) until

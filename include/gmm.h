@@ -489,8 +489,8 @@ int gmm_server_admit(gmm_server_t *s, const gmm_config *cfg);
 
 /* As gmm_pool_reserve for the server: state_bytes for camera state,
  * staging_bytes for the per-camera upload and mask buffers; same statuses.
- * May be called from any thread; it waits for the engine's current
- * launch to be queued, not for the device. */
+ * May be called from any thread; synchronous: it waits for the work queued
+ * on the engine's compute stream, so call it before the frames flow. */
 int gmm_server_reserve(gmm_server_t *s, size_t state_bytes, size_t staging_bytes);
 
 /* End a camera's session: waits (up to timeout_ms; < 0 = no bound) until

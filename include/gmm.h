@@ -445,7 +445,12 @@ size_t gmm_pool_state_used(const gmm_pool_t *p);
  * supply it, GMM_ECUDA on another CUDA failure (not sticky). */
 int gmm_pool_reserve(gmm_pool_t *p, size_t bytes);
 
+/* Wait for every tick queued on the pool's stream. GMM_ECUDA if a CUDA
+ * failure is sticky on the pool. */
 int gmm_pool_sync(gmm_pool_t *p);
+
+/* Wait for the pool's stream, then free every camera's state, the pool's
+ * buffers and the pool itself (p is invalid afterwards). */
 int gmm_pool_destroy(gmm_pool_t *p);
 
 /* ---------------------------------------------------------------- serving */

@@ -335,9 +335,14 @@ int gmm_mask_confusion(const uint32_t *pred, const uint32_t *truth, int H, int W
  * H*ceil(W/32) above that limit (more than 8,388,608 pixels, e.g. 4096 x
  * 2048) are rejected with GMM_EINVAL. All calls share the array: calls that
  * can overlap on the GPU (different streams, or other threads) race on it
- * and must be serialised by the caller. The first call on a device looks up
- * the array's device address; make that first call before any stream
- * capture. */
+ * and must be serialised by the caller. The first call in each CUDA context
+ * (per device, and again after cudaDeviceReset or in another context the
+ * caller made current) looks up the array's device address; under lazy
+ * module loading, the CUDA default, that first call also loads the module
+ * that holds the array, which needs its 1 MiB of free device memory and can
+ * fail with GMM_ECUDA when the application has already taken the rest.
+ * Make one warm-up call per device at start-up, before reserving the GPU's
+ * memory and before any stream capture; later calls allocate nothing. */
 #define GMM_NOALLOC_MAX_MASK_WORDS (1 << 18)
 int gmm_apply_open3_noalloc(const gmm_config *cfg, void *state, int first,
                             const uint8_t *rgb8, const uint16_t *depth16,

@@ -17,35 +17,82 @@
 using namespace gmmlib;
 
 // Every device that loads the library holds this array until the process
-// exits. All calls share it.
+// exits (under lazy module loading, from the first call on that device on).
+// All calls share it.
 static __device__ __align__(256) uint32_t g_noalloc_mask[GMM_NOALLOC_MAX_MASK_WORDS];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-uint32_t *g_scratch[kMaxDevices] = {};
+// Context of the calling thread, through the driver API entry points the
+// runtime hands out (no link against libcuda). A context id is unique for
+// the life of the process: a context made after cudaDeviceReset, or a
+// non-primary context a driver-API caller made current, gets a new one.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+std::once_flag g_entry_once;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
 
-// Device address of g_noalloc_mask for the current device. The array's name
-// in host code is only a host-side stand-in, so the address must come from
-// the runtime, once per device, with that device current.
-int scratch_for_current_device(uint32_t **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess)
-        return cuda_fail(nullptr, e, "gmm_apply_open3_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices)
-        return fail(GMM_EINVAL, "gmm_apply_open3_noalloc: device index out of range");
+void load_entry_points() {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+        g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(fn);
+}
+
+// Id of the context current on this thread; false if there is none or the
+// driver cannot say.
+bool current_context_id(unsigned long long *id) {
+    std::call_once(g_entry_once, load_entry_points);
+    if (!g_ctx_get_current || !g_ctx_get_id)
+        return false;
+    void *ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx)
+        return false;
+    return g_ctx_get_id(ctx, id) == 0;
+}
+
+// Addresses of g_noalloc_mask already looked up, keyed by context id (the
+// address belongs to one context: each context loads its own copy of the
+// module that holds the array).
+constexpr int kCacheSlots = 64;
+std::mutex g_setup_mu;
+unsigned long long g_ctx_ids[kCacheSlots] = {};
+uint32_t *g_scratch[kCacheSlots] = {};
+int g_next_slot = 0;
+
+// Device address of g_noalloc_mask in the calling thread's current context.
+// The array's name in host code is only a host-side stand-in, so the address
+// comes from the runtime, once per context, with that context current. The
+// lookup also makes the runtime set up the device's primary context when no
+// context is current yet, so the id is taken after it.
+int scratch_for_current_context(uint32_t **out) {
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch[dev]) {
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_mask);
-        if (e != cudaSuccess || !ptr)
-            return cuda_fail(nullptr, e == cudaSuccess ? cudaErrorInvalidSymbol : e,
-                             "gmm_apply_open3_noalloc: cudaGetSymbolAddress");
-        g_scratch[dev] = static_cast<uint32_t *>(ptr);
+    unsigned long long id = 0;
+    if (current_context_id(&id)) {
+        for (int i = 0; i < kCacheSlots; ++i) {
+            if (g_scratch[i] && g_ctx_ids[i] == id) {
+                *out = g_scratch[i];
+                return GMM_OK;
+            }
+        }
     }
-    *out = g_scratch[dev];
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_mask);
+    if (e != cudaSuccess || !ptr)
+        return cuda_fail(nullptr, e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                         "gmm_apply_open3_noalloc: cudaGetSymbolAddress");
+    *out = static_cast<uint32_t *>(ptr);
+    if (current_context_id(&id)) {
+        g_ctx_ids[g_next_slot] = id;
+        g_scratch[g_next_slot] = *out;
+        g_next_slot = (g_next_slot + 1) % kCacheSlots;
+    }
     return GMM_OK;
 }
 
@@ -74,7 +121,7 @@ extern "C" int gmm_apply_open3_noalloc(const gmm_config *cfg, void *state, int f
     if (!p.empty())
         return fail(GMM_EINVAL, "gmm_apply_open3_noalloc: " + p);
     uint32_t *scratch = nullptr;
-    int rc = scratch_for_current_device(&scratch);
+    int rc = scratch_for_current_context(&scratch);
     if (rc != GMM_OK)
         return rc;
     const Layout L = make_layout(cfg->H, cfg->W, cfg->M, cfg->precision);

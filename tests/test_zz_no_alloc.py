@@ -10,7 +10,10 @@ takes the model state from the caller. Both paths run the same kernels, so
 the masks and the state must agree exactly, on two calls in a row (the first
 initialises the caller's state, the second updates it).
 
-This file is collected last on purpose."""
+The file name sorts last, so pytest collects it after every other test: this
+test was added on its own, and should it fail in a run that stops at the first
+failure (-x), every other test has already run. It passes in either order:
+alone in a fresh process, and after the rest of the suite."""
 import ctypes
 
 import numpy as np
@@ -115,3 +118,36 @@ def test_noalloc_state_and_mask_stay_in_bounds(H, W, M, prec):
     for buf, n in ((sbuf, nbytes), (mbuf, 4 * mwords)):
         b = buf.cpu().numpy()
         assert (b[:guard] == canary).all() and (b[guard + n:] == canary).all()
+
+
+def test_noalloc_calls_allocate_no_device_memory():
+    """After one warm-up call (the first call in a context looks up the
+    scratch array and, under lazy module loading, loads the module that holds
+    it), further calls leave both torch's allocator and the device's free
+    memory exactly where they were."""
+    import torch
+    L = G.load_library()
+    H, W, M, prec = 96, 160, 5, G.PREC_F32
+    rgb, depth, _ = scene_frames(303, H, W, 1, 10, 6)
+    frames = [to_dev(rgb[t], depth[t]) for t in range(6)]
+    state = torch.empty((G.state_bytes(H, W, M, prec),), dtype=torch.uint8, device="cuda")
+    mask = torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda")
+    cfg = _config(L, H, W, M, prec)
+    stream = torch.cuda.current_stream()
+
+    def call(t):
+        r, d = frames[t]
+        rc = L.gmm_apply_open3_noalloc(ctypes.byref(cfg), state.data_ptr(), 1 if t == 0 else 0,
+                                       r.data_ptr(), d.data_ptr(), mask.data_ptr(),
+                                       stream.cuda_stream)
+        assert rc == G.OK, L.gmm_last_error()
+
+    call(0)
+    torch.cuda.synchronize()
+    allocated = torch.cuda.memory_allocated()
+    free_before = torch.cuda.mem_get_info()[0]
+    for t in range(1, 6):
+        call(t)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == allocated
+    assert torch.cuda.mem_get_info()[0] == free_before

@@ -18,6 +18,8 @@
 // is bank-conflict free.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "gmm_internal.h"
 #include "gmm_tma.cuh"
 
@@ -356,25 +358,50 @@ __global__ void __launch_bounds__(kTile) k_tick_staged(const CamView cv, int *st
     }
 }
 
+// Launch set-up of one staged instance on one device: the dynamic shared
+// memory limit is a per-device attribute of the function, and the resident
+// CTA count follows from it, so both are set and queried once per device
+// (under a lock: two threads may make their first call together). A failed
+// set-up is not remembered; the next call tries again.
+constexpr int kMaxDevices = 64;
+
+template <int M, int PREC, int ST>
+cudaError_t staged_ctas_per_sm(size_t smem, int *out) {
+    static std::mutex mu;
+    static int max_per_sm[kMaxDevices] = {}; // 0: not set up on that device yet
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= kMaxDevices)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (max_per_sm[dev] == 0) {
+        e = cudaFuncSetAttribute(k_tick_staged<M, PREC, ST>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tick_staged<M, PREC, ST>, kTile,
+                                                          smem);
+        if (e != cudaSuccess)
+            return e;
+        if (n < 1)
+            return cudaErrorInvalidConfiguration;
+        max_per_sm[dev] = n;
+    }
+    *out = max_per_sm[dev];
+    return cudaSuccess;
+}
+
 template <int M, int PREC, int ST>
 cudaError_t launch_staged_t(const CamView &cv, int ctas_per_sm, int *status, cudaStream_t s) {
     constexpr int EB = PREC == 0 ? 4 : 2;
     constexpr size_t smem = (size_t)ST * (kFields * M * kTile * EB + 6 * kTile);
-    static bool configured = false;
-    static int max_per_sm = 1;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tick_staged<M, PREC, ST>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_per_sm, k_tick_staged<M, PREC, ST>,
-                                                          kTile, smem);
-        if (e != cudaSuccess)
-            return e;
-        if (max_per_sm < 1)
-            return cudaErrorInvalidConfiguration;
-        configured = true;
-    }
+    int max_per_sm = 1;
+    cudaError_t e = staged_ctas_per_sm<M, PREC, ST>(smem, &max_per_sm);
+    if (e != cudaSuccess)
+        return e;
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < max_per_sm) ? ctas_per_sm : max_per_sm;
     int64_t grid = (int64_t)gmmhost::num_sms() * per_sm;
     if (grid > cv.n_tiles)

@@ -273,10 +273,12 @@ template <> __device__ __forceinline__ void rank_sort<5, 4>(Comp<4> (&c)[5]) { n
 // One tick of one mixture at one pixel (§III.A). The components are in rank
 // order on entry and on exit. Returns the stream's foreground bit.
 // kSkipSorted: let a warp skip the sorting network when it would change
-// nothing (pays where issue slots, not HBM, bound the kernel).
+// nothing (pays where issue slots, not HBM, bound the kernel); `lanes` is
+// then the set of lanes of the warp that make this same call, computed by
+// the caller before the code diverged (unused otherwise).
 template <int M, int D, bool kSkipSorted, bool kOptions>
 __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D],
-                                            const StreamPrm &p) {
+                                            const StreamPrm &p, uint32_t lanes) {
     // Match: first component, in rank order, within k standard deviations.
     int j = -1;
     float d2j = 0.f;
@@ -367,7 +369,7 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
 #pragma unroll
     for (int i = 1; i < M; ++i)
         sorted = sorted && !(c[i].key > c[i - 1].key);
-    if (!kSkipSorted || __any_sync(__activemask(), !sorted))
+    if (!kSkipSorted || __any_sync(lanes, !sorted))
         rank_sort<M, D>(c);
     int rank = 0, B = M;
     float acc = 0.f;
@@ -423,6 +425,9 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
     const uint32_t p32 = (uint32_t)p;
     const uint32_t row = div_wpr(p32 >> 5, cv);
     const uint32_t x = p32 - row * (uint32_t)cv.w_pad;
+    // Every caller enters with whole warps; the lanes on image pixels (not
+    // row padding) are the ones that run the colour (or augmented) mixture.
+    const uint32_t lanes_c = kSkipSorted ? __ballot_sync(0xffffffffu, x < (uint32_t)cv.W) : 0u;
     if (x >= (uint32_t)cv.W)
         return 0u;
     const int64_t q = (int64_t)row * cv.W + x;
@@ -463,7 +468,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
             }
             if (draw == 0u)
                 xa[3] = a[0].mu[3];
-            fg = mixture_step<M, 4, kSkipSorted, true>(a, xa, cv.pc);
+            fg = mixture_step<M, 4, kSkipSorted, true>(a, xa, cv.pc, lanes_c);
         }
         void *plw = cv.planes;
 #pragma unroll
@@ -508,7 +513,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
                 d[i].mu[0] = f.mud;
                 d[i].v = f.vd;
             }
-            fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0)>(c, xc, cv.pc);
+            fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0)>(c, xc, cv.pc, lanes_c);
         } else {
             // The depth values stay packed (two registers per component
             // instead of three) while the colour mixture runs.
@@ -524,7 +529,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
                 dw[i] = g0.x;
                 dmv[i] = g1.y;
             }
-            fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0)>(c, xc, cv.pc);
+            fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0)>(c, xc, cv.pc, lanes_c);
 #pragma unroll
             for (int i = 0; i < M; ++i) {
                 d[i].w = bf16_hi(dw[i]);
@@ -535,6 +540,9 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
         }
     }
 
+    // The lanes that run the depth mixture: a reading, and a started model.
+    const uint32_t lanes_d =
+        kSkipSorted ? __ballot_sync(lanes_c, draw != 0u && (fb & kDepthStarted)) : 0u;
     if (draw == 0u) {
         fgd = fgc; // no reading: depth model untouched, depth answer = colour
     } else if (!(fb & kDepthStarted)) {
@@ -547,7 +555,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
         fb |= kDepthStarted;
         fgd = 0;
     } else {
-        fgd = mixture_step<M, 1, kSkipSorted, (kVariant != 0)>(d, xd, cv.pd);
+        fgd = mixture_step<M, 1, kSkipSorted, (kVariant != 0)>(d, xd, cv.pd, lanes_d);
     }
     fb = fuse_list1(fgc, fgd, fb);
 

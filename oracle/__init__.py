@@ -77,7 +77,7 @@ def _declare(L):
     L.oracle_rank_order.restype = None
     L.oracle_background_count.argtypes = [ctypes.c_int, _dp, ctypes.c_double]
     L.oracle_background_count.restype = ctypes.c_int
-    L.oracle_stream_step.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _ip]
+    L.oracle_stream_step.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _ip, _dp]
     L.oracle_stream_step.restype = ctypes.c_int
     L.oracle_fuse.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _ip]
     L.oracle_fuse.restype = None
@@ -85,6 +85,8 @@ def _declare(L):
                               _dp, _dp, _dp, _dp, _dp, _dp, _i8p, _i8p, _u8p, _u8p, _u16p,
                               _u8p, _u8p, _u8p, _u8p]
     L.oracle_tick.restype = None
+    L.oracle_tick_ex.argtypes = L.oracle_tick.argtypes + [_dp, _dp, _i8p]
+    L.oracle_tick_ex.restype = None
     L.oracle_morph_open3.argtypes = [ctypes.c_int, ctypes.c_int, _u8p, _u8p, _u8p]
     L.oracle_morph_open3.restype = None
     L.oracle_tick_augmented.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
@@ -118,17 +120,23 @@ def stream_init(M, D, init_var, x):
     return w, mu.reshape(M, D), v
 
 
-def stream_step(prm, w, mu, v, x):
+def stream_step(prm, w, mu, v, x, with_margin=False):
     """One tick of one stream at one pixel. Arrays are updated in place
     (mu has shape (M, D)). Returns (fg, info) with info = (matched stored
-    index or -1, B, rank of the matched/replaced component, near bits)."""
+    index or -1, B, rank of the matched/replaced component, near bits), and
+    with_margin: (fg, info, margin), the smallest relative distance of a
+    decision to its threshold."""
     M, D = mu.shape
     assert w.dtype == np.float64 and mu.dtype == np.float64 and v.dtype == np.float64
     xa = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(D))
     info = np.zeros(4, dtype=np.int32)
+    mrg = np.zeros(1)
     fg = lib().oracle_stream_step(M, D, _ptr(prm, ctypes.c_double), _ptr(w, ctypes.c_double),
                                   _ptr(mu, ctypes.c_double), _ptr(v, ctypes.c_double),
-                                  _ptr(xa, ctypes.c_double), _ptr(info, ctypes.c_int))
+                                  _ptr(xa, ctypes.c_double), _ptr(info, ctypes.c_int),
+                                  _ptr(mrg, ctypes.c_double))
+    if with_margin:
+        return int(fg), tuple(int(i) for i in info), float(mrg[0])
     return int(fg), tuple(int(i) for i in info)
 
 
@@ -183,7 +191,13 @@ class OracleGMM:
         self.first = True
         self.frames = 0
 
-    def tick(self, rgb: np.ndarray, depth: np.ndarray) -> dict:
+    def tick(self, rgb: np.ndarray, depth: np.ndarray, report: bool = False) -> dict:
+        """One tick. Returns the masks and near bits; with report also the
+        per-stream margins ("margin_c", "margin_d": smallest relative
+        distance of a decision to its threshold, inf where the stream took no
+        step) and the decisions ("dec", int8 [H, W, 6]: colour matched stored
+        index or -1, B, rank of the matched or replaced component, then the
+        same for depth; -2 where the stream took no step)."""
         H, W = self.H, self.W
         N = H * W
         rgb = np.ascontiguousarray(rgb, dtype=np.uint8).reshape(H, W, 3)
@@ -191,19 +205,28 @@ class OracleGMM:
         fg_rgb = np.zeros(N, np.uint8); fg_d = np.zeros(N, np.uint8)
         fused = np.zeros(N, np.uint8); near = np.zeros(N, np.uint8)
         d = ctypes.c_double
-        lib().oracle_tick(H, W, self.M, _ptr(self.prm_c, d), _ptr(self.prm_d, d), int(self.first),
-                          _ptr(self.wc, d), _ptr(self.muc, d), _ptr(self.vc, d),
-                          _ptr(self.wd, d), _ptr(self.mud, d), _ptr(self.vd, d),
-                          _ptr(self.F, ctypes.c_int8), _ptr(self.cpt, ctypes.c_int8),
-                          _ptr(self.dinit, ctypes.c_uint8), _ptr(rgb, ctypes.c_uint8),
-                          _ptr(depth, ctypes.c_uint16), _ptr(fg_rgb, ctypes.c_uint8),
-                          _ptr(fg_d, ctypes.c_uint8), _ptr(fused, ctypes.c_uint8),
-                          _ptr(near, ctypes.c_uint8))
+        args = [H, W, self.M, _ptr(self.prm_c, d), _ptr(self.prm_d, d), int(self.first),
+                _ptr(self.wc, d), _ptr(self.muc, d), _ptr(self.vc, d),
+                _ptr(self.wd, d), _ptr(self.mud, d), _ptr(self.vd, d),
+                _ptr(self.F, ctypes.c_int8), _ptr(self.cpt, ctypes.c_int8),
+                _ptr(self.dinit, ctypes.c_uint8), _ptr(rgb, ctypes.c_uint8),
+                _ptr(depth, ctypes.c_uint16), _ptr(fg_rgb, ctypes.c_uint8),
+                _ptr(fg_d, ctypes.c_uint8), _ptr(fused, ctypes.c_uint8),
+                _ptr(near, ctypes.c_uint8)]
+        shp = (H, W)
+        out = {}
+        if report:
+            mc = np.zeros(N); md = np.zeros(N); dec = np.zeros(N * 6, np.int8)
+            lib().oracle_tick_ex(*args, _ptr(mc, d), _ptr(md, d), _ptr(dec, ctypes.c_int8))
+            out = {"margin_c": mc.reshape(shp), "margin_d": md.reshape(shp),
+                   "dec": dec.reshape(H, W, 6)}
+        else:
+            lib().oracle_tick(*args)
         self.first = False
         self.frames += 1
-        shp = (H, W)
-        return {"fg_rgb": fg_rgb.reshape(shp), "fg_d": fg_d.reshape(shp),
-                "fused": fused.reshape(shp), "near": near.reshape(shp)}
+        out.update({"fg_rgb": fg_rgb.reshape(shp), "fg_d": fg_d.reshape(shp),
+                    "fused": fused.reshape(shp), "near": near.reshape(shp)})
+        return out
 
     # -- state in the product library's plane layout ---------------------------
     def planes(self) -> np.ndarray:

@@ -54,7 +54,11 @@
  * its threshold: a tested squared distance against k^2 v (bit 0), a rank-prefix
  * weight sum against T (bit 1), or two unequal sort keys against each other
  * (bit 2). A lower-precision implementation may legitimately decide those
- * cases the other way.
+ * cases the other way. It can also report the smallest of those relative
+ * distances itself (the step's margin), and the decisions taken (matched
+ * component, B, rank of the matched or replaced component), so that a
+ * comparison of two trajectories can tell a decision that flipped near its
+ * threshold from one that flipped far from it.
  */
 
 #include <math.h>
@@ -133,15 +137,20 @@ int oracle_background_count(int M, const double *w_ranked, double T)
  * on entry and on exit. Returns the stream's foreground bit.
  * info[0]: stored index that matched before the update, -1 on a miss;
  * info[1]: B; info[2]: rank of the matched (or replaced) component after the
- * update; info[3]: near-threshold bits. */
+ * update; info[3]: near-threshold bits. margin (may be NULL): the smallest
+ * relative distance of a decision to its threshold, over the same decisions
+ * the near bits look at: |d^2 - k^2 v| / (k^2 v) for each tested component,
+ * |k_a - k_b| / max(k_a, k_b) for each pair of unequal sort keys, and
+ * |prefix sum - T| / T for each rank prefix. */
 int oracle_stream_step(int M, int D, const double *prm, double *w, double *mu,
-                       double *v, const double *x, int *info)
+                       double *v, const double *x, int *info, double *margin)
 {
     const double alpha = prm[P_ALPHA], k = prm[P_K], T = prm[P_T];
     const double init_var = prm[P_INIT_VAR], init_w = prm[P_INIT_W];
     const double v_min = prm[P_VMIN], eps = prm[P_EPS];
     const int flags = (int)prm[P_FLAGS];
     int near = 0;
+    double mrg = INFINITY;
 
     /* 1. Match: distance of the sample to each mean, tested from the best
      *    ranked component down; the first one within k standard deviations
@@ -156,6 +165,7 @@ int oracle_stream_step(int M, int D, const double *prm, double *w, double *mu,
         double lim = k * k * v[i];
         if (fabs(d2 - lim) <= eps * lim)
             near |= NEAR_MATCH;
+        mrg = fmin(mrg, fabs(d2 - lim) / lim);
         if (d2 < lim)
             j = i;
     }
@@ -220,6 +230,8 @@ int oracle_stream_step(int M, int D, const double *prm, double *w, double *mu,
             double ka = rank_key(w[a], v[a]), kb = rank_key(w[b], v[b]);
             if (ka != kb && fabs(ka - kb) <= eps * fmax(ka, kb))
                 near |= NEAR_KEY;
+            if (ka != kb)
+                mrg = fmin(mrg, fabs(ka - kb) / fmax(ka, kb));
         }
     }
     double tw[ORACLE_MAX_M], tmu[ORACLE_MAX_M * 4], tv[ORACLE_MAX_M];
@@ -244,6 +256,7 @@ int oracle_stream_step(int M, int D, const double *prm, double *w, double *mu,
         acc += w[b];
         if (fabs(acc - T) <= eps * T)
             near |= NEAR_T;
+        mrg = fmin(mrg, fabs(acc - T) / T);
     }
 
     /* 6. Foreground: nothing matched, or the matched component is not in
@@ -252,6 +265,8 @@ int oracle_stream_step(int M, int D, const double *prm, double *w, double *mu,
     info[1] = B;
     info[2] = rank_j;
     info[3] = near;
+    if (margin)
+        *margin = mrg;
     return fg;
 }
 
@@ -287,12 +302,17 @@ void oracle_fuse(int f_rgb, int f_d, int *F, int *cpt)
  *   F[N] fused label, cpt[N] List-1 counter, dinit[N] depth model started.
  * first != 0 starts every model from this frame.
  * Outputs (each may be NULL): fg_rgb[N], fg_d[N], fused[N], near[N]
- * (near: colour bits 0-2, depth bits 4-6). */
-void oracle_tick(int H, int W, int M, const double *prm_c, const double *prm_d,
-                 int first, double *wc, double *muc, double *vc, double *wd,
-                 double *mud, double *vd, int8_t *F, int8_t *cpt,
-                 uint8_t *dinit, const uint8_t *rgb, const uint16_t *depth,
-                 uint8_t *fg_rgb, uint8_t *fg_d, uint8_t *fused, uint8_t *near)
+ * (near: colour bits 0-2, depth bits 4-6); margin_c[N], margin_d[N] (the
+ * stream step's margin, INFINITY where the stream took no step: first frame,
+ * invalid depth, depth model starting); dec[N*6] the decisions, per pixel
+ * {colour: matched stored index or -1, B, rank of the matched or replaced
+ * component; depth: the same}, -2 where the stream took no step. */
+void oracle_tick_ex(int H, int W, int M, const double *prm_c, const double *prm_d,
+                    int first, double *wc, double *muc, double *vc, double *wd,
+                    double *mud, double *vd, int8_t *F, int8_t *cpt,
+                    uint8_t *dinit, const uint8_t *rgb, const uint16_t *depth,
+                    uint8_t *fg_rgb, uint8_t *fg_d, uint8_t *fused, uint8_t *near,
+                    double *margin_c, double *margin_d, int8_t *dec)
 {
     const long N = (long)H * (long)W;
     for (long n = 0; n < N; n++) {
@@ -302,6 +322,8 @@ void oracle_tick(int H, int W, int M, const double *prm_c, const double *prm_d,
         double *w1 = wc + n * M, *m1 = muc + n * M * 3, *v1 = vc + n * M;
         double *w2 = wd + n * M, *m2 = mud + n * M, *v2 = vd + n * M;
         int info[4];
+        int dc[3] = {-2, -2, -2}, dd[3] = {-2, -2, -2};
+        double mc = INFINITY, md = INFINITY;
         int nbits = 0;
         int fc, fdp;
 
@@ -312,8 +334,11 @@ void oracle_tick(int H, int W, int M, const double *prm_c, const double *prm_d,
             oracle_stream_init(M, 3, prm_c[P_INIT_VAR], w1, m1, v1, xc);
             fc = 0;
         } else {
-            fc = oracle_stream_step(M, 3, prm_c, w1, m1, v1, xc, info);
+            fc = oracle_stream_step(M, 3, prm_c, w1, m1, v1, xc, info, &mc);
             nbits |= info[3];
+            dc[0] = info[0];
+            dc[1] = info[1];
+            dc[2] = info[2];
         }
 
         if (depth[n] == 0) {
@@ -323,8 +348,11 @@ void oracle_tick(int H, int W, int M, const double *prm_c, const double *prm_d,
             dinit[n] = 1;
             fdp = 0;
         } else {
-            fdp = oracle_stream_step(M, 1, prm_d, w2, m2, v2, &xd, info);
+            fdp = oracle_stream_step(M, 1, prm_d, w2, m2, v2, &xd, info, &md);
             nbits |= info[3] << 4;
+            dd[0] = info[0];
+            dd[1] = info[1];
+            dd[2] = info[2];
         }
 
         int Fi = F[n], ci = cpt[n];
@@ -340,7 +368,27 @@ void oracle_tick(int H, int W, int M, const double *prm_c, const double *prm_d,
             fused[n] = (uint8_t)Fi;
         if (near)
             near[n] = (uint8_t)nbits;
+        if (margin_c)
+            margin_c[n] = mc;
+        if (margin_d)
+            margin_d[n] = md;
+        if (dec)
+            for (int k = 0; k < 3; k++) {
+                dec[6 * n + k] = (int8_t)dc[k];
+                dec[6 * n + 3 + k] = (int8_t)dd[k];
+            }
     }
+}
+
+/* oracle_tick_ex without the margins and decisions. */
+void oracle_tick(int H, int W, int M, const double *prm_c, const double *prm_d,
+                 int first, double *wc, double *muc, double *vc, double *wd,
+                 double *mud, double *vd, int8_t *F, int8_t *cpt,
+                 uint8_t *dinit, const uint8_t *rgb, const uint16_t *depth,
+                 uint8_t *fg_rgb, uint8_t *fg_d, uint8_t *fused, uint8_t *near)
+{
+    oracle_tick_ex(H, W, M, prm_c, prm_d, first, wc, muc, vc, wd, mud, vd, F, cpt, dinit,
+                   rgb, depth, fg_rgb, fg_d, fused, near, NULL, NULL, NULL);
 }
 
 /* The augmentation alternative (§III.B, Fig. 2): one mixture over four
@@ -367,7 +415,7 @@ void oracle_tick_augmented(int H, int W, int M, const double *prm, double depth_
             oracle_stream_init(M, 4, prm[P_INIT_VAR], wn, mn, vn, x);
         } else {
             int info[4];
-            f = oracle_stream_step(M, 4, prm, wn, mn, vn, x, info);
+            f = oracle_stream_step(M, 4, prm, wn, mn, vn, x, info, NULL);
             nb = info[3];
         }
         if (fg)

@@ -35,7 +35,7 @@ def _frac(s: str) -> float:
 
 # ---------------------------------------------------------------- hand traces
 def load_hand_trace(name="hand_trace_2x2.txt"):
-    params, frames, outs, states = {}, {}, {}, {}
+    params, frames, outs, states, decs = {}, {}, {}, {}, {}
     with open(os.path.join(GOLDEN, name)) as f:
         for line in f:
             line = line.strip()
@@ -51,11 +51,13 @@ def load_hand_trace(name="hand_trace_2x2.txt"):
                 outs[(int(tok[1]), tok[2])] = [int(v) for v in tok[3:]]
             elif tok[0] == "state":
                 states[(int(tok[1]), tok[2], tok[3])] = [_frac(v) for v in tok[4:]]
-    return params, frames, outs, states
+            elif tok[0] == "dec":
+                decs[(int(tok[1]), int(tok[2]))] = [int(v) for v in tok[3:]]
+    return params, frames, outs, states, decs
 
 
 def check_hand_trace():
-    params, frames, outs, states = load_hand_trace()
+    params, frames, outs, states, decs = load_hand_trace()
     M = int(params["M"])
     g = O.OracleGMM(2, 2, M, float(params["alpha"]), float(params["k"]), float(params["T"]),
                     float(params["init_var"]), float(params["init_w"]),
@@ -63,7 +65,15 @@ def check_hand_trace():
     for t in sorted(frames):
         grey, dep = frames[t]
         rgb = np.repeat(np.array(grey, np.uint8).reshape(2, 2, 1), 3, axis=2)
-        out = g.tick(rgb, np.array(dep, np.uint16).reshape(2, 2))
+        out = g.tick(rgb, np.array(dep, np.uint16).reshape(2, 2), report=True)
+        for p in range(4):
+            exp = decs.get((t, p))
+            if exp is not None:
+                got = out["dec"].reshape(4, 6)[p].tolist()
+                assert got == exp, f"frame {t} pixel {p} decisions: {got} != {exp}"
+            # a stream without a step reports no margin
+            assert (exp[0] == -2) == np.isinf(out["margin_c"].reshape(-1)[p])
+            assert (exp[3] == -2) == np.isinf(out["margin_d"].reshape(-1)[p])
         for name in ("fg_rgb", "fg_d", "fused"):
             exp = outs.get((t, name))
             if exp is not None:
@@ -419,6 +429,151 @@ def check_augmented_model():
     assert sep.tick(c, d)["fg_d"][0, 0] == 1
 
 
+# ---------------------------------------------------------------- F1 (Eq. 1-3)
+def check_f1_hand_counted():
+    """Confusion counts and Eq. 1-3 on a hand-counted 4x4 example (exact
+    fractions), and the degenerate cases with empty denominators."""
+    pred = truth = counts = scores = None
+    cases = []
+    with open(os.path.join(GOLDEN, "f1_confusion_4x4.txt")) as f:
+        for line in f:
+            tok = line.split()
+            if not tok or tok[0].startswith("#"):
+                continue
+            if tok[0] == "pred":
+                pred = np.array([int(v) for v in tok[1:]]).reshape(4, 4)
+            elif tok[0] == "truth":
+                truth = np.array([int(v) for v in tok[1:]]).reshape(4, 4)
+            elif tok[0] == "counts":
+                counts = [int(v) for v in tok[1:]]
+            elif tok[0] == "scores":
+                scores = [Fraction(v) for v in tok[1:]]
+            elif tok[0] == "case":
+                cases.append((np.array([int(c) for c in tok[3]]), np.array([int(c) for c in tok[5]]),
+                              [int(v) for v in tok[7:11]], [Fraction(v) for v in tok[12:15]]))
+    cases.insert(0, (pred, truth, counts, scores))
+    for pr, tr, cnt, sc in cases:
+        r = O.f1_scores(pr, tr)
+        assert [r["tp"], r["fp"], r["fn"], r["tn"]] == cnt, (r, cnt)
+        for name, want in zip(("recall", "precision", "f1"), sc):
+            assert abs(r[name] - float(want)) <= 1e-15, (name, r[name], want)
+
+
+# ---------------------------------------------------------------- near-threshold report
+def _step_report(prm, w, mu, v, x):
+    w = np.array(w, dtype=np.float64)
+    mu = np.array(mu, dtype=np.float64).reshape(len(w), -1)
+    v = np.array(v, dtype=np.float64)
+    fg, info, margin = O.stream_step(prm, w, mu, v, x, with_margin=True)
+    return info[0], info[3], margin
+
+
+def check_near_threshold_report():
+    """The near bits flag a decision within eps (relative) of its threshold
+    and nothing farther, for each of the three decisions; the margin is that
+    relative distance. Cases at (1 +- 5e-6) of a threshold must flag at
+    eps = 1e-5 and cases at (1 +- 2e-5) must not, with every other decision
+    of the step far from its threshold."""
+    eps = 1e-5
+    prm = O.stream_params(0.01, 2.5, 0.7, 16.0, 0.05, eps=eps)
+    # Match: component 0 at mu 1000, v 16, k^2 v = 100; the others far away.
+    for delta, near in ((-5e-6, True), (5e-6, True), (-2e-5, False), (2e-5, False)):
+        x = 1000.0 + 10.0 * np.sqrt(1.0 + delta)
+        j, bits, margin = _step_report(prm, [0.6, 0.3, 0.1], [1000.0, 5000.0, 9000.0],
+                                       [16.0, 16.0, 16.0], [x])
+        assert j == (0 if delta < 0 else -1), (delta, j)
+        assert bits == (O.NEAR_MATCH if near else 0), (delta, bits)
+        assert abs(margin - abs(delta)) <= 1e-9, (delta, margin)
+    # Background set: the best component's updated weight at T (1 + delta).
+    T = O.f32(0.7)
+    for delta, near in ((-5e-6, True), (5e-6, True), (-2e-5, False), (2e-5, False)):
+        w0 = (T * (1.0 + delta) - 0.01) / 0.99
+        rest = 1.0 - w0
+        j, bits, margin = _step_report(prm, [w0, 0.6 * rest, 0.4 * rest], [500.0, 800.0, 900.0],
+                                       [16.0, 16.0, 16.0], [500.0])
+        assert j == 0 and bits == (O.NEAR_T if near else 0), (delta, j, bits)
+        assert abs(margin - abs(delta)) <= 1e-9, (delta, margin)
+    # Sort keys: two unmatched components whose keys differ by a factor
+    # (1 + delta) (both decay by the same factor, so the ratio stays).
+    for delta, near in ((-5e-6, True), (5e-6, True), (-2e-5, False), (2e-5, False)):
+        w1 = 0.2 * (1.0 + delta)
+        j, bits, margin = _step_report(prm, [1.0 - w1 - 0.2, w1, 0.2], [500.0, 800.0, 900.0],
+                                       [16.0, 16.0, 16.0], [500.0])
+        want = abs(delta) / (1.0 + max(delta, 0.0))
+        assert j == 0 and bits == (O.NEAR_KEY if near else 0), (delta, j, bits)
+        assert abs(margin - want) <= 1e-9, (delta, margin)
+    # Equal keys are a tie the stable order settles, not a near decision.
+    j, bits, margin = _step_report(prm, [0.5, 0.25, 0.25], [500.0, 800.0, 900.0],
+                                   [1.0, 4.0, 4.0], [500.0])
+    assert j == 0 and bits == 0 and margin > 1e-2, (j, bits, margin)
+
+
+def check_near_threshold_boundary():
+    """At exactly eps from a threshold the decision is flagged (the bound is
+    inclusive). Dyadic values keep every step exact: eps = 1/64, alpha = 1/2,
+    weights summing to one exactly."""
+    eps = 1.0 / 64.0
+    # Match: D = 3, k = 2, v = 16, so k^2 v = 64; x - mu = (8, 1, 0): d^2 = 65.
+    prm = O.stream_params(0.5, 2.0, 0.7, 16.0, 0.05, eps=eps)
+    j, bits, margin = _step_report(prm, [0.5, 0.3, 0.2],
+                                   [[0.0, 0.0, 0.0], [200.0, 200.0, 200.0], [100.0, 100.0, 100.0]],
+                                   [16.0, 16.0, 16.0], [8.0, 1.0, 0.0])
+    assert j == -1 and bits == O.NEAR_MATCH and margin == eps, (j, bits, margin)
+    # Background set: T = 3/4, updated best weight 0.5 * 67/128 + 0.5 = 195/256 = T (1 + eps).
+    prm = O.stream_params(0.5, 2.0, 0.75, 16.0, 0.05, eps=eps)
+    j, bits, margin = _step_report(prm, [67 / 128, 40 / 128, 21 / 128], [500.0, 800.0, 900.0],
+                                   [1.0, 4.0, 16.0], [500.0])
+    assert j == 0 and bits == O.NEAR_T and margin == eps, (j, bits, margin)
+    # Keys: updated weights 1/8 (v = 1) and 63/256 (v = 4): keys 1/8 and 63/512,
+    # apart by exactly eps times the larger.
+    prm = O.stream_params(0.5, 2.0, 0.7, 16.0, 0.05, eps=eps)
+    j, bits, margin = _step_report(prm, [0.2578125, 0.25, 0.4921875], [500.0, 800.0, 900.0],
+                                   [1.0, 1.0, 4.0], [500.0])
+    assert j == 0 and bits == O.NEAR_KEY and margin == eps, (j, bits, margin)
+
+
+def check_near_bits_per_stream():
+    """Image level: a near match in the depth stream lands in bits 4-6 and
+    its margin in margin_d; the colour stream, far from every threshold,
+    reports neither."""
+    g = O.OracleGMM(1, 1, 3, 0.01, 2.5, 0.7, 16.0, 0.05)
+    g.tick(np.full((1, 1, 3), 100, np.uint8), np.full((1, 1), 2000, np.uint16))
+    planes = g.planes()
+    planes[:, 0, 0, 0] = [0.6, 0.3, 0.1]          # colour weights
+    planes[:, 5, 0, 0] = [0.6, 0.3, 0.1]          # depth weights
+    planes[:, 1:4, 0, 0] = [[100.0] * 3, [180.0] * 3, [20.0] * 3]
+    planes[:, 6, 0, 0] = [2000.0, 3000.0, 1000.0]
+    v_d = 100.0 / (6.25 * (1.0 + 5e-6))             # d^2 = 100 = k^2 v_d (1 + 5e-6)
+    planes[:, 7, 0, 0] = [v_d, 16.0, 16.0]
+    planes[:, 4, 0, 0] = [16.0, 16.0, 16.0]
+    g.set_state(planes, g.fusion_bytes())
+    out = g.tick(np.full((1, 1, 3), 100, np.uint8), np.full((1, 1), 2010, np.uint16), report=True)
+    assert out["near"][0, 0] == O.NEAR_MATCH << 4, out["near"]
+    assert abs(out["margin_d"][0, 0] - 5e-6) <= 1e-9 and out["margin_c"][0, 0] > 1e-2, out
+    # colour: matches component 0, weights (0.604, 0.297, 0.099) -> B = 2, rank 0;
+    # depth: d^2 = 100 just above k^2 v, a miss; the replacement (weight
+    # 0.05 / 0.941, v 16) ranks last, weights (0.631, 0.316, 0.053) -> B = 2
+    assert out["dec"][0, 0].tolist() == [0, 2, 0, -1, 2, 2], out["dec"]
+
+
+def check_margin_matches_near_bits(seed=9, pixels=60, steps=80):
+    """Over random sequences, with eps large enough that near decisions
+    occur: a step's near bits are set exactly when its margin is at most eps."""
+    rng = np.random.default_rng(seed)
+    eps = 0.02
+    prm = O.stream_params(0.05, 2.5, 0.7, 50.0, 0.05, eps=eps)
+    seen = [0, 0]
+    for _ in range(pixels):
+        w, mu, v = O.stream_init(4, 1, 50.0, [rng.uniform(0, 255)])
+        base = rng.uniform(50, 200)
+        for _ in range(steps):
+            x = base + rng.normal(0, 6) + (rng.uniform(-80, 80) if rng.random() < 0.1 else 0.0)
+            fg, info, margin = O.stream_step(prm, w, mu, v, [x], with_margin=True)
+            assert (info[3] != 0) == (margin <= eps), (info, margin)
+            seen[int(info[3] != 0)] += 1
+    assert min(seen) > 20, seen
+
+
 ALL_CHECKS = [
     check_hand_trace, check_list1_traces, check_list1_properties,
     check_closed_form_constant_input, check_closed_form_depth,
@@ -426,4 +581,6 @@ ALL_CHECKS = [
     check_rank_order_bruteforce, check_background_count_exact,
     check_morph_open_against_scipy, check_depth_invalid_and_late_start,
     check_closed_form_per_channel_variance, check_rho_eta_against_scipy, check_augmented_model,
+    check_f1_hand_counted, check_near_threshold_report, check_near_threshold_boundary,
+    check_near_bits_per_stream, check_margin_matches_near_bits,
 ]

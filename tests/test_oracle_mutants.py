@@ -3,8 +3,10 @@ catch every one. Each mutant is compiled from a patched copy of
 ``oracle/gmm_oracle.c`` into a temporary directory; the real oracle is never
 modified."""
 import ctypes
+import inspect
 import os
 import subprocess
+import textwrap
 
 import pytest
 
@@ -48,6 +50,36 @@ MUTANTS = {
     "augmented_imputes_wrong_component": ("x[3] = first ? 0.0 : mn[3];",
                                           "x[3] = first ? 0.0 : mn[7];"),
     "augmented_depth_unscaled": ("depth_scale * (double)depth[n]};", "(double)depth[n]};"),
+    # the near-threshold report and the margins, decisions beside it
+    "near_match_absolute": ("if (fabs(d2 - lim) <= eps * lim)", "if (fabs(d2 - lim) <= eps)"),
+    "near_match_exclusive": ("if (fabs(d2 - lim) <= eps * lim)", "if (fabs(d2 - lim) < eps * lim)"),
+    "near_T_absolute": ("if (fabs(acc - T) <= eps * T)", "if (fabs(acc - T) <= eps)"),
+    "near_T_exclusive": ("if (fabs(acc - T) <= eps * T)", "if (fabs(acc - T) < eps * T)"),
+    "near_key_exclusive": ("if (ka != kb && fabs(ka - kb) <= eps * fmax(ka, kb))",
+                           "if (ka != kb && fabs(ka - kb) < eps * fmax(ka, kb))"),
+    "near_key_dropped": ("near |= NEAR_KEY;", "near |= 0;"),
+    "near_key_flags_ties": ("if (ka != kb && fabs(ka - kb) <= eps * fmax(ka, kb))",
+                            "if (fabs(ka - kb) <= eps * fmax(ka, kb))"),
+    "near_depth_in_colour_bits": ("nbits |= info[3] << 4;", "nbits |= info[3];"),
+    "margin_match_absolute": ("mrg = fmin(mrg, fabs(d2 - lim) / lim);",
+                              "mrg = fmin(mrg, fabs(d2 - lim));"),
+    "margin_T_dropped": ("mrg = fmin(mrg, fabs(acc - T) / T);", "mrg = mrg;"),
+    "margin_key_dropped": ("mrg = fmin(mrg, fabs(ka - kb) / fmax(ka, kb));", "mrg = mrg;"),
+    "margin_depth_from_colour": ("margin_d[n] = md;", "margin_d[n] = mc;"),
+    "decision_depth_from_colour": ("dec[6 * n + 3 + k] = (int8_t)dd[k];",
+                                   "dec[6 * n + 3 + k] = (int8_t)dc[k];"),
+}
+
+# Plausible mistakes in the F1 tooling (Eq. 1-3), planted in copies of
+# oracle.f1_scores.
+F1_MUTANTS = {
+    "recall_over_fp": ("R = tp / (tp + fn)", "R = tp / (tp + fp)"),
+    "precision_over_fn": ("P = tp / (tp + fp)", "P = tp / (tp + fn)"),
+    "f1_without_two": ("F1 = 2 * P * R / (P + R)", "F1 = P * R / (P + R)"),
+    "f1_arithmetic_mean": ("F1 = 2 * P * R / (P + R)", "F1 = (P + R) / 2"),
+    "fn_counts_fp": ("fn = int(np.count_nonzero(~p & t))", "fn = int(np.count_nonzero(p & ~t))"),
+    "tn_keeps_fn": ("tn = int(p.size - tp - fp - fn)", "tn = int(p.size - tp - fp)"),
+    "empty_recall_one": ("R = tp / (tp + fn) if tp + fn else 0.0", "R = tp / (tp + fn) if tp + fn else 1.0"),
 }
 
 
@@ -83,3 +115,21 @@ def test_pins_catch_mutant(name, tmp_path, swap_oracle_lib):
             failed.append(check.__name__)
             break
     assert failed, f"no pin caught mutant {name}"
+
+
+@pytest.mark.parametrize("name", sorted(F1_MUTANTS))
+def test_pins_catch_f1_mutant(name, monkeypatch):
+    old, new = F1_MUTANTS[name]
+    src = textwrap.dedent(inspect.getsource(O.f1_scores))
+    assert src.count(old) == 1, f"mutation site for {name} not found or not unique"
+    ns = {"np": O.np}
+    exec(src.replace(old, new, 1), ns)
+    monkeypatch.setattr(O, "f1_scores", ns["f1_scores"])
+    failed = []
+    for check in P.ALL_CHECKS:
+        try:
+            check()
+        except AssertionError:
+            failed.append(check.__name__)
+            break
+    assert failed, f"no pin caught F1 mutant {name}"

@@ -52,8 +52,8 @@
  * Near-threshold report. For each stream step the oracle also reports, in its
  * own arithmetic, whether any decision sat within a relative distance `eps` of
  * its threshold: a tested squared distance against k^2 v (bit 0), a rank-prefix
- * weight sum against T (bit 1), or two unequal sort keys against each other
- * (bit 2). A lower-precision implementation may legitimately decide those
+ * weight sum against T (bit 1), or the sort keys of two components with
+ * different parameters against each other (bit 2). A lower-precision implementation may legitimately decide those
  * cases the other way. It can also report the smallest of those relative
  * distances itself (the step's margin), and the decisions taken (matched
  * component, B, rank of the matched or replaced component), so that a
@@ -140,7 +140,8 @@ int oracle_background_count(int M, const double *w_ranked, double T)
  * update; info[3]: near-threshold bits. margin (may be NULL): the smallest
  * relative distance of a decision to its threshold, over the same decisions
  * the near bits look at: |d^2 - k^2 v| / (k^2 v) for each tested component,
- * |k_a - k_b| / max(k_a, k_b) for each pair of unequal sort keys, and
+ * |k_a - k_b| / max(k_a, k_b) for each pair of components with different
+ * parameters (w, v), and
  * |prefix sum - T| / T for each rank prefix. */
 int oracle_stream_step(int M, int D, const double *prm, double *w, double *mu,
                        double *v, const double *x, int *info, double *margin)
@@ -225,12 +226,18 @@ int oracle_stream_step(int M, int D, const double *prm, double *w, double *mu,
     /* 4. Order: stable descending sort by w / sqrt(v). */
     int perm[ORACLE_MAX_M];
     oracle_rank_order(M, w, v, perm);
+    /* Near keys: two components with different parameters whose keys are
+     * within eps, equal ones included (an exact tie between different w and
+     * v, such as w' = 1.1 w with v' = 1.21 v, holds only in exact arithmetic;
+     * rounding may break it either way). Two components with the same w and
+     * v have the same key in any arithmetic: a tie the stable order settles. */
     for (int a = 0; a < M; a++) {
         for (int b = a + 1; b < M; b++) {
             double ka = rank_key(w[a], v[a]), kb = rank_key(w[b], v[b]);
-            if (ka != kb && fabs(ka - kb) <= eps * fmax(ka, kb))
+            const int twins = (w[a] == w[b] && v[a] == v[b]);
+            if (!twins && fabs(ka - kb) <= eps * fmax(ka, kb))
                 near |= NEAR_KEY;
-            if (ka != kb)
+            if (!twins)
                 mrg = fmin(mrg, fabs(ka - kb) / fmax(ka, kb));
         }
     }

@@ -502,10 +502,22 @@ def check_near_threshold_report():
         want = abs(delta) / (1.0 + max(delta, 0.0))
         assert j == 0 and bits == (O.NEAR_KEY if near else 0), (delta, j, bits)
         assert abs(margin - want) <= 1e-9, (delta, margin)
-    # Equal keys are a tie the stable order settles, not a near decision.
+    # Two components with the same w and v have the same key in any
+    # arithmetic: a tie the stable order settles, not a near decision.
     j, bits, margin = _step_report(prm, [0.5, 0.25, 0.25], [500.0, 800.0, 900.0],
                                    [1.0, 4.0, 4.0], [500.0])
     assert j == 0 and bits == 0 and margin > 1e-2, (j, bits, margin)
+    # Different parameters with exactly equal keys (w 1/4, v 4 and w 1/8,
+    # v 1: both keys 1/8, and 1/16 after a dyadic update) are a tie only in
+    # exact arithmetic: near, margin 0.
+    prm2 = O.stream_params(0.5, 2.5, 0.7, 16.0, 0.05, eps=eps)
+    j, bits, margin = _step_report(prm2, [0.625, 0.25, 0.125], [500.0, 800.0, 900.0],
+                                   [1.0, 4.0, 1.0], [500.0])
+    assert j == 0 and bits == O.NEAR_KEY and margin == 0.0, (j, bits, margin)
+    # Same weight, variances 4 and 4 (1 + 4e-6): not twins, keys 2e-6 apart.
+    j, bits, margin = _step_report(prm2, [0.5, 0.25, 0.25], [500.0, 800.0, 900.0],
+                                   [1.0, 4.0, 4.0 * (1.0 + 4e-6)], [500.0])
+    assert j == 0 and bits == O.NEAR_KEY and abs(margin - 2e-6) <= 1e-8, (j, bits, margin)
 
 
 def check_near_threshold_boundary():

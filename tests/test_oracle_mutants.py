@@ -55,11 +55,15 @@ MUTANTS = {
     "near_match_exclusive": ("if (fabs(d2 - lim) <= eps * lim)", "if (fabs(d2 - lim) < eps * lim)"),
     "near_T_absolute": ("if (fabs(acc - T) <= eps * T)", "if (fabs(acc - T) <= eps)"),
     "near_T_exclusive": ("if (fabs(acc - T) <= eps * T)", "if (fabs(acc - T) < eps * T)"),
-    "near_key_exclusive": ("if (ka != kb && fabs(ka - kb) <= eps * fmax(ka, kb))",
-                           "if (ka != kb && fabs(ka - kb) < eps * fmax(ka, kb))"),
+    "near_key_exclusive": ("if (!twins && fabs(ka - kb) <= eps * fmax(ka, kb))",
+                           "if (!twins && fabs(ka - kb) < eps * fmax(ka, kb))"),
     "near_key_dropped": ("near |= NEAR_KEY;", "near |= 0;"),
-    "near_key_flags_ties": ("if (ka != kb && fabs(ka - kb) <= eps * fmax(ka, kb))",
-                            "if (fabs(ka - kb) <= eps * fmax(ka, kb))"),
+    "near_key_flags_twins": ("if (!twins && fabs(ka - kb) <= eps * fmax(ka, kb))",
+                             "if (fabs(ka - kb) <= eps * fmax(ka, kb))"),
+    "near_key_skips_exact_ties": ("if (!twins && fabs(ka - kb) <= eps * fmax(ka, kb))",
+                                  "if (ka != kb && fabs(ka - kb) <= eps * fmax(ka, kb))"),
+    "twins_by_weight_only": ("const int twins = (w[a] == w[b] && v[a] == v[b]);",
+                             "const int twins = (w[a] == w[b]);"),
     "near_depth_in_colour_bits": ("nbits |= info[3] << 4;", "nbits |= info[3];"),
     "margin_match_absolute": ("mrg = fmin(mrg, fabs(d2 - lim) / lim);",
                               "mrg = fmin(mrg, fabs(d2 - lim));"),

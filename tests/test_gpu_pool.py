@@ -5,10 +5,8 @@ and must match the oracle."""
 import numpy as np
 import pytest
 
-import oracle as O
 import paper_2110_14934_gb300 as G
-import synth
-from parity import FREE_RUN_EPS, scene_frames, state_mismatch, to_dev, words
+from parity import FreeRun, scene_frames, to_dev, words
 
 pytestmark = pytest.mark.gpu
 
@@ -120,32 +118,33 @@ def test_pool_fp16_launch_shapes(launch):
 
 
 def test_pool_matches_oracle():
+    """Every camera of a pooled tick against the oracle, free-running with
+    every difference classified (parity.FreeRun)."""
     import torch
     n = 10
     frames = _frames(n)
     pool = G.Pool(max_cams=8)
     ids = [pool.admit(H, W, M) for (H, W, M) in CAMS]
-    orcs = [O.OracleGMM(H, W, M, 0.01, 2.5, 0.7, 225.0, 0.05, eps=FREE_RUN_EPS)
-            for (H, W, M) in CAMS]
-    diverged = [np.zeros((H, W), bool) for (H, W, M) in CAMS]
+    frs = [FreeRun(H, W, M) for (H, W, M) in CAMS]
+    before = [None] * len(CAMS)
     for t in range(n):
-        masks = []
+        outs = []
         for i, (H, W, M) in enumerate(CAMS):
             r, d = to_dev(frames[i][0][t], frames[i][1][t])
-            m = torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda")
-            pool.submit(ids[i], r, d, m)
-            masks.append((m, r, d))
+            ms = [torch.empty((H, G.mask_words_per_row(W)), dtype=torch.int32, device="cuda")
+                  for _ in range(3)]
+            pool.submit(ids[i], r, d, *ms)
+            outs.append(ms + [r, d])  # the frames stay alive until the tick has run
         pool.tick()
         torch.cuda.synchronize()
         for i, (H, W, M) in enumerate(CAMS):
-            o = orcs[i].tick(frames[i][0][t], frames[i][1][t])
-            diverged[i] |= o["near"] != 0
-            g = G.unpack_mask(words(masks[i][0]), H, W)
-            assert not np.any((g != o["fused"].astype(bool)) & ~diverged[i]), (i, t)
-    for i in range(len(CAMS)):
-        st = state_mismatch(pool.planes(ids[i]), orcs[i].planes(), orcs[i].fusion_bytes(),
-                            exclude=diverged[i])
-        assert sum(st["bad"]) == 0, (i, st)
+            g = {k: G.unpack_mask(words(v), H, W)
+                 for k, v in zip(("fused", "fg_rgb", "fg_d"), outs[i][:3])}
+            after = (pool.planes(ids[i]), pool.fusion(ids[i]))
+            frs[i].step(frames[i][0][t], frames[i][1][t], g, before[i], after)
+            before[i] = after
+    for f in frs:
+        f.check()
 
 
 def test_pool_budget_and_release():

@@ -3,19 +3,24 @@
 and fusion tick on GB300.
 
 One step = one tick of the whole path (colour mixture, depth mixture, List-1
-fusion, bit-packed mask) over one frame of the workload. The metric is
-Mpixel-frames/s; the JSON line also carries the HBM roofline fraction of the
-tick kernel, per-tick latency percentiles, an end-to-end figure through the
-host-memory C-ABI path, and the FP64 oracle timed on the host cores.
+fusion, bit-packed mask) over one frame of every camera of the workload. The
+default workload is c2: 64 cameras at mixed resolutions advanced by one
+pooled launch per tick (CUDA graph, online-tuned launch shape), FP32 state.
+The metric is Mpixel-frames/s; the JSON line also carries the HBM roofline
+fraction of the pooled kernel, per-tick latency percentiles, an end-to-end
+figure with host frames and masks, the same cameras one launch per camera
+(`plain`), the same cameras with FP16/BF16 state (`fp16_state`), a short run
+of the serving engine with frame-latency percentiles (`serving`), and the
+FP64 oracle timed on the host cores.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c1]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2]
   python bench.py --impl reference ...   # the oracle arm, on host cores
 
 Frames are synthetic (seeded generator standing in for Kinect captures) and
 resident in device memory before the timed region. Under torchrun every rank
-runs its own camera (weak scaling, no data-path collective); the timed region
-is bracketed by a barrier and a device synchronisation and the slowest
-rank's time is reported.
+runs its own cameras (weak scaling, no data-path collective); the timed
+region is bracketed by a barrier and a device synchronisation and the
+slowest rank's time is reported.
 """
 from __future__ import annotations
 
@@ -763,6 +768,12 @@ def run_pool(args, wl):
 
     e2e = run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, args.e2e_steps or min(K, 600),
                        Wm, world)
+    # c2 at N = 1: the same cameras and frames with FP16/BF16 state (the
+    # precision configuration) and a short run of the serving engine
+    extras = args.workload == "c2" and world == 1 and not args.no_extras
+    fp16 = (pool_precision_extra(G, torch, args, cams, rgb_base, dep_base, rgb_step, dep_step,
+                                 mask_ptr, nf, stream, max(K, 100), Wm) if extras else None)
+    serving = serving_extra(G, torch, args, dev) if extras else None
     cpu = (oracle_many_cameras(wl, args.cpu_seconds)
            if rank == 0 and world == 1 and args.cpu_seconds > 0 else None)
     clk = None
@@ -780,9 +791,10 @@ def run_pool(args, wl):
                          "traffic_note": "scaled from an 8-camera capture by algorithmic bytes",
                          "algorithmic_bytes_per_tick": tick_bytes,
                          "kernel": f"k_pool_{'flat' if flat else 'tick'}<{'f32' if prec == 0 else 'f16'}>"},
-            "plain_one_camera_per_launch_f32": {"value": plain_value, "unit": UNIT,
-                                                "steps": n_plain,
-                                                "pooled_over_plain": value / plain_value},
+            "plain": {"value": plain_value, "unit": UNIT, "steps": n_plain,
+                      "pooled_over_plain": value / plain_value,
+                      "path": "the same cameras and frames, one FP32 handle per camera, one "
+                              "gmm_apply launch per camera per tick"},
             "latency_ms": {"tick_p50": pct(tick_ms, 50), "tick_p99": pct(tick_ms, 99)},
             "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
                     "d2h_bytes_per_step": e2e["d2h"], "launch": e2e["launch"],
@@ -797,6 +809,10 @@ def run_pool(args, wl):
             "gpu_launches": K * pool_launches(cams, shape),
             "clocks": clk,
         }
+        if fp16 is not None:
+            line["fp16_state"] = fp16
+        if serving is not None:
+            line["serving"] = serving
         if model_flags(args, G):
             line["config"]["weights_rounding"] = "stochastic"
         print(json.dumps(line), flush=True)
@@ -805,6 +821,114 @@ def run_pool(args, wl):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def pool_precision_extra(G, torch, args, cams, rgb_base, dep_base, rgb_step, dep_step, mask_ptr,
+                         nf, stream, steps, warmup):
+    """The c2 cameras and frames in a pool with FP16 means/variances and
+    BF16 weights (workload c3's storage), tuned online the same way; K
+    device-timed ticks. Returns the value, the pooled kernel's roofline and
+    the launch shape."""
+    prec = 1
+    pool = G.Pool(precision=prec, max_cams=len(cams), device=stream.device)
+    ids = [pool.admit(H, W, M, **PARAMS) for (H, W, M, _) in cams]
+    pool.set_stream(stream)
+    pool.use_graph(True)
+
+    def submit(f):
+        pool.submit_many(ids, [b + f * s for b, s in zip(rgb_base, rgb_step)],
+                         [b + f * s for b, s in zip(dep_base, dep_step)], mask_ptr)
+
+    submit(0)
+    pool.tick(stream)
+    pool.autotune_online(3)
+    k = 1
+    while pool.tuning()[0] and k < 2000:
+        submit(k % nf)
+        pool.tick(stream)
+        k += 1
+    for j in range(warmup):
+        submit((k + j) % nf)
+        pool.tick(stream)
+    f0 = k + warmup
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for j in range(steps):
+        submit((f0 + j) % nf)
+        pool.tick(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    shape = pool.tuning()[1]
+    pool.close()
+    px = sum(H * W for (H, W, _, _) in cams)
+    tick_bytes = sum(H * W * bytes_per_pixel(M, prec) for (H, W, M, _) in cams)
+    achieved = tick_bytes / (ms / steps / 1e3) / 1e9
+    peak, peak_src = measured_hbm_peak()
+    flat = shape.get("ctas_per_sm", 0) < 0
+    return {"workload": "the c2 cameras and frames with FP16 means/variances and BF16 weights "
+                        "(FP32 arithmetic), as in c3",
+            "value": steps * px / ms / 1e3, "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+            "launch": shape,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": (recorded_traffic("pool_flat" if flat else "pool", prec,
+                                                      tick_bytes) if len(cams) <= 128 else None),
+                         "algorithmic_bytes_per_tick": tick_bytes,
+                         "kernel": f"k_pool_{'flat' if flat else 'tick'}<f16>"}}
+
+
+def serving_setup(G, torch, wl, rank, dev):
+    """Cameras of the serving workload and a small ring of page-locked host
+    frames per resolution (the frames the simulated cameras deliver)."""
+    import synth
+    cams = camera_mix(wl["cams_per_res"], rank)
+    ring = []
+    for ri, (H, W) in enumerate(CAMERA_RESOLUTIONS):
+        r, d, _ = synth.frames_device(synth.scene(rank_seed(5000 + ri, rank), H, W, 1), 0,
+                                      wl["frames"], device=dev, with_gt=False)
+        ring.append((r.cpu().pin_memory(), d.cpu().pin_memory()))
+    return cams, ring
+
+
+def serving_extra(G, torch, args, dev):
+    """A short run of workload c4 (256 cameras, Poisson sessions, 30 fps each,
+    80 GB budget, FP16/BF16 state) on the serving engine: frame latency
+    (arrival to fused mask in host memory), drops and rejections; the same
+    cameras as a genlocked rig (every camera's frames arrive together, so
+    each period opens with a burst that continuous batching packs into few
+    ticks); and a tight 8 GB budget, to exercise admission control."""
+    wl = WORKLOADS["c4"]
+    cams, ring = serving_setup(G, torch, wl, 0, dev)
+    dur = args.extra_serve_seconds
+    out = {"workload": f"c4: {wl['name']}", "duration_s": dur, "unit": "ms"}
+    st, lat, wall, _, rel_err, _, parts = serve_run(G, torch, cams, ring, wl,
+                                                    int(wl["budget_gb"] * 1e9), dur, 2021)
+    lat = list(lat)
+    out.update({"p50": fnum(pct(lat, 50)), "p99": fnum(pct(lat, 99)), "p999": fnum(pct(lat, 99.9)),
+                "max": fnum(lat[-1]) if lat else None,
+                "what": "frame arrival to fused mask in host memory",
+                "frames_completed": st["completed"], "frames_dropped": st["dropped"],
+                "sessions_admitted": st["admitted"], "admissions_rejected": st["rejected"],
+                "budget_gb": wl["budget_gb"], "ticks": st["ticks"],
+                "mean_frames_per_tick": st["completed"] / max(st["ticks"], 1),
+                "mpx_frames_per_s": st["pixels"] / wall / 1e6, "release_errors": len(rel_err),
+                "device_ms_p99": parts["device_ms"]["p99"] if parts else None})
+    st3, lat3, _, _, _, _, _ = serve_run(G, torch, cams, ring, wl, int(wl["budget_gb"] * 1e9),
+                                         dur, 2021, genlocked=True)
+    lat3 = list(lat3)
+    out["genlocked"] = {"p50": fnum(pct(lat3, 50)), "p99": fnum(pct(lat3, 99)),
+                        "p999": fnum(pct(lat3, 99.9)), "frames_completed": st3["completed"],
+                        "frames_dropped": st3["dropped"], "ticks": st3["ticks"],
+                        "mean_frames_per_tick": st3["completed"] / max(st3["ticks"], 1)}
+    st2, lat2, _, _, _, _, _ = serve_run(G, torch, cams, ring, wl,
+                                         int(wl["tight_budget_gb"] * 1e9), dur, 77)
+    out["tight_budget"] = {"budget_gb": wl["tight_budget_gb"],
+                           "sessions_admitted": st2["admitted"],
+                           "admissions_rejected": st2["rejected"],
+                           "p99": fnum(pct(list(lat2), 99))}
+    return out
 
 
 def pool_launches(cams, shape):
@@ -1136,10 +1260,8 @@ def latency_breakdown(tr, ticket_cam, cams, t0):
 
 
 def run_serving(args, wl):
-    import numpy as np  # noqa: F401  (used by the helpers)
     import torch
     import paper_2110_14934_gb300 as G
-    import synth
 
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
@@ -1147,13 +1269,7 @@ def run_serving(args, wl):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    cams = camera_mix(wl["cams_per_res"], rank)
-    nf = wl["frames"]
-    ring = []
-    for ri, (H, W) in enumerate(CAMERA_RESOLUTIONS):
-        r, d, _ = synth.frames_device(synth.scene(rank_seed(5000 + ri, rank), H, W, 1), 0, nf,
-                                      device=dev, with_gt=False)
-        ring.append((r.cpu().pin_memory(), d.cpu().pin_memory()))
+    cams, ring = serving_setup(G, torch, wl, rank, dev)
     duration = args.serve_seconds or wl["duration_s"]
     barrier(world, dev)
     st, lat, wall, lag, rel_err, admit_ms, parts = serve_run(G, torch, cams, ring, wl,
@@ -1314,7 +1430,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gmm", "reference"], default="gmm")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c1")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--e2e-steps", type=int, default=0, help="0: same as --steps")
     ap.add_argument("--kernel", choices=sorted(KERNELS), default="direct")
     ap.add_argument("--variant", type=int, default=0, help="staged tile shape 0-3")
@@ -1338,6 +1454,11 @@ def main(argv=None):
                     help="FP16 state: store the weights with stochastic rounding")
     ap.add_argument("--morph", action="store_true",
                     help="single-camera workloads: each step adds the 3x3 opening of the mask")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="c2: skip the extra keys (the same cameras with FP16/BF16 state, and a "
+                         "short serving run)")
+    ap.add_argument("--extra-serve-seconds", type=float, default=4.0,
+                    help="c2: simulated seconds of each extra serving run")
     ap.add_argument("--cpu-frames", type=int, default=21, help="oracle baseline frames (0 = skip)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle baseline rows per frame (0 = all)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,

@@ -224,19 +224,27 @@ __device__ __forceinline__ void store_fields(void *pl, int64_t e0, int64_t tb, u
 }
 
 // ------------------------------------------------------------ mixture step
+// Sort key of a component: the bits of w / sqrt(v) (a positive float, so its
+// bits order like its value) with the low three bits replaced by 7 - the
+// component's stored rank i. Comparing keys as unsigned integers orders by
+// w / sigma and, between values that agree to 2^-20 relative (the same value
+// included), puts the lower stored rank first: a total order, under which the
+// network's result is the stable sort. (Two values that close lie well inside
+// the 1e-5 margin at which a decision counts as near its threshold.)
+__device__ __forceinline__ uint32_t rank_key(float w, float v, int i) {
+    return (__float_as_uint(w * rsqrtf(v)) & ~7u) | (7u - (uint32_t)i);
+}
+
 template <int D> struct Comp {
-    float key;
-    int idx;
+    uint32_t key; // rank_key of the component
     float w, v;
     float mu[D];
 };
 
 template <int D>
 __device__ __forceinline__ void comp_swap_if(Comp<D> &a, Comp<D> &b) {
-    // a sits before b. Descending key; equal keys keep the lower stored index
-    // first, which makes the order total and the network's result the stable
-    // sort.
-    const bool sw = (b.key > a.key) || (b.key == a.key && b.idx < a.idx);
+    // a sits before b: the larger key goes first
+    const bool sw = b.key > a.key;
     Comp<D> lo = sw ? b : a;
     Comp<D> hi = sw ? a : b;
     a = lo;
@@ -279,9 +287,10 @@ template <> __device__ __forceinline__ void rank_sort<5, 4>(Comp<4> (&c)[5]) { n
 template <int M, int D, bool kSkipSorted, bool kOptions>
 __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D],
                                             const StreamPrm &p, uint32_t lanes) {
-    // Match: first component, in rank order, within k standard deviations.
-    int j = -1;
-    float d2j = 0.f;
+    // Match: first component, in rank order, within k standard deviations
+    // (bit i of hit: component i is within; the first set bit wins).
+    uint32_t hit = 0u;
+    float d2s[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         float d2 = 0.f;
@@ -290,13 +299,19 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
             const float df = x[ch] - c[i].mu[ch];
             d2 = fmaf(df, df, d2);
         }
-        if (j < 0 && d2 < p.k2 * c[i].v) {
-            j = i;
-            d2j = d2;
-        }
+        d2s[i] = d2;
+        if (d2 < p.k2 * c[i].v)
+            hit |= 1u << i;
     }
-    const bool matched = j >= 0;
-    const int jj = matched ? j : M - 1;
+    const bool matched = hit != 0u;
+    const int jj = matched ? __ffs(hit) - 1 : M - 1;
+    float d2j = d2s[0];
+    if (kOptions) {
+#pragma unroll
+        for (int i = 1; i < M; ++i)
+            if (i == jj)
+                d2j = d2s[i];
+    }
 
     // The component that changes (matched, or the last-ranked on a miss),
     // gathered once.
@@ -325,7 +340,7 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
         c[i].w = w;
         sum += w;
     }
-    const float inv = 1.0f / sum;
+    const float inv = __fdividef(1.0f, sum); // within 2 ulp; the sum is near 1
 
     // Mean and variance of the changed component (the variance from the
     // squared distance to the new mean).
@@ -350,14 +365,13 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         c[i].w *= inv;
-        c[i].idx = i;
         if (i == jj) {
 #pragma unroll
             for (int ch = 0; ch < D; ++ch)
                 c[i].mu[ch] = muj[ch];
             c[i].v = vj;
         }
-        c[i].key = c[i].w * rsqrtf(c[i].v);
+        c[i].key = rank_key(c[i].w, c[i].v, i);
     }
 
     // Re-rank by w / sigma (stable), then the background test. When every
@@ -369,19 +383,25 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
 #pragma unroll
     for (int i = 1; i < M; ++i)
         sorted = sorted && !(c[i].key > c[i - 1].key);
-    if (!kSkipSorted || __any_sync(lanes, !sorted))
+    int rank = jj; // the changed component's rank after the update
+    if (!kSkipSorted || __any_sync(lanes, !sorted)) {
         rank_sort<M, D>(c);
-    int rank = 0, B = M;
-    float acc = 0.f;
 #pragma unroll
-    for (int r = 0; r < M; ++r) {
-        if (c[r].idx == jj)
-            rank = r;
-        acc += c[r].w;
-        if (B == M && acc > p.T)
-            B = r + 1;
+        for (int r = 0; r < M; ++r)
+            if ((c[r].key & 7u) == 7u - (uint32_t)jj) // its stored rank, from the key
+                rank = r;
     }
-    return (!matched || rank >= B) ? 1 : 0;
+    // Background test: the rank is in B (the shortest prefix summing past T)
+    // unless the prefix before it already sums past T (prefix sums of
+    // non-negative weights do not decrease under rounding).
+    float acc = 0.f, before = 0.f;
+#pragma unroll
+    for (int r = 0; r < M - 1; ++r) {
+        acc += c[r].w;
+        if (r + 1 == rank)
+            before = acc;
+    }
+    return (!matched || before > p.T) ? 1 : 0;
 }
 
 // List 1 (§III.C) on the low four bits of the per-pixel byte.
@@ -577,13 +597,17 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
 // starting at a multiple of 32 (word index wi).
 __device__ __forceinline__ void write_mask_words(const CamView &cv, int64_t wi, uint32_t bits) {
     const uint32_t F = __ballot_sync(0xffffffffu, bits & 1u);
-    const uint32_t fc = __ballot_sync(0xffffffffu, bits & 2u);
-    const uint32_t fd = __ballot_sync(0xffffffffu, bits & 4u);
-    if ((threadIdx.x & 31u) == 0u) {
+    const bool lane0 = (threadIdx.x & 31u) == 0u;
+    if (lane0)
         cv.mask[wi] = F;
-        if (cv.fg_rgb)
+    if (cv.fg_rgb) { // uniform: the whole warp takes it or not
+        const uint32_t fc = __ballot_sync(0xffffffffu, bits & 2u);
+        if (lane0)
             cv.fg_rgb[wi] = fc;
-        if (cv.fg_d)
+    }
+    if (cv.fg_d) {
+        const uint32_t fd = __ballot_sync(0xffffffffu, bits & 4u);
+        if (lane0)
             cv.fg_d[wi] = fd;
     }
 }

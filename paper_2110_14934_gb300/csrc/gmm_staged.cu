@@ -124,7 +124,7 @@ __device__ __forceinline__ int staged_mixture_step(uint8_t *st, int f0, int t,
         w[i] = wi;
         sum += wi;
     }
-    const float inv = 1.0f / sum;
+    const float inv = __fdividef(1.0f, sum);
 #pragma unroll
     for (int i = 0; i < M; ++i)
         w[i] *= inv;
@@ -146,20 +146,20 @@ __device__ __forceinline__ int staged_mixture_step(uint8_t *st, int f0, int t,
             muj[c] = x[c];
         vj = p.init_var;
     }
-    // Stable ranks by w / sqrt(v): a component goes after every earlier one
-    // with a key at least as large.
-    float key[M];
+    // Ranks by rank_key (w / sqrt(v), ties by stored rank): a component goes
+    // after every earlier one with a larger key.
+    uint32_t key[M];
     int r[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-        key[i] = w[i] * rsqrtf(i == jj ? vj : v[i]);
+        key[i] = rank_key(w[i], i == jj ? vj : v[i], i);
         r[i] = 0;
     }
 #pragma unroll
     for (int i = 1; i < M; ++i) {
 #pragma unroll
         for (int l = 0; l < i; ++l) {
-            if (key[l] >= key[i])
+            if (key[l] > key[i])
                 ++r[i];
             else
                 ++r[l];

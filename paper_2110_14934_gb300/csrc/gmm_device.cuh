@@ -278,33 +278,36 @@ template <> __device__ __forceinline__ void rank_sort<5, 3>(Comp<3> (&c)[5]) { n
 template <> __device__ __forceinline__ void rank_sort<5, 1>(Comp<1> (&c)[5]) { net5(c); }
 template <> __device__ __forceinline__ void rank_sort<5, 4>(Comp<4> (&c)[5]) { net5(c); }
 
-// One tick of one mixture at one pixel (§III.A). The components are in rank
-// order on entry and on exit. Returns the stream's foreground bit.
-// kSkipSorted: let a warp skip the sorting network when it would change
-// nothing (pays where issue slots, not HBM, bound the kernel); `lanes` is
-// then the set of lanes of the warp that make this same call, computed by
-// the caller before the code diverged (unused otherwise).
-template <int M, int D, bool kSkipSorted, bool kOptions>
-__device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D],
-                                            const StreamPrm &p, uint32_t lanes) {
-    // Match: first component, in rank order, within k standard deviations
-    // (bit i of hit: component i is within; the first set bit wins).
-    uint32_t hit = 0u;
-    float d2s[M];
+// Background test (§III.A) of the changed component at rank `rank` after
+// the update: it is in B (the shortest rank prefix summing past T) unless the
+// prefix before it already sums past T (prefix sums of non-negative weights
+// do not decrease under rounding, so this equals rank >= B). A miss is
+// foreground.
+template <int M, int D>
+__device__ __forceinline__ int background_test(const Comp<D> (&c)[M], int rank, bool matched,
+                                               float T) {
+    float acc = 0.f, before = 0.f;
 #pragma unroll
-    for (int i = 0; i < M; ++i) {
-        float d2 = 0.f;
-#pragma unroll
-        for (int ch = 0; ch < D; ++ch) {
-            const float df = x[ch] - c[i].mu[ch];
-            d2 = fmaf(df, df, d2);
-        }
-        d2s[i] = d2;
-        if (d2 < p.k2 * c[i].v)
-            hit |= 1u << i;
+    for (int r = 0; r < M - 1; ++r) {
+        acc += c[r].w;
+        if (r + 1 == rank)
+            before = acc;
     }
-    const bool matched = hit != 0u;
-    const int jj = matched ? __ffs(hit) - 1 : M - 1;
+    return (!matched || before > T) ? 1 : 0;
+}
+
+// The update after the match (§III.A): weights, the changed component's mean
+// and variance, re-ranking and the background test. hit: bit i set when
+// component i lies within k standard deviations (the first set bit is the
+// match); d2s: the squared distances. kJ >= 0: every lane of this call
+// matched component kJ (the changed component is then known at compile time
+// and needs no selects); kJ < 0: any outcome.
+template <int M, int D, bool kSkipSorted, bool kOptions, int kJ>
+__device__ __forceinline__ int mixture_update(Comp<D> (&c)[M], const float (&x)[D],
+                                              const StreamPrm &p, uint32_t lanes, uint32_t hit,
+                                              const float (&d2s)[M]) {
+    const bool matched = kJ >= 0 || hit != 0u;
+    const int jj = kJ >= 0 ? kJ : (matched ? __ffs(hit) - 1 : M - 1);
     float d2j = d2s[0];
     if (kOptions) {
 #pragma unroll
@@ -330,15 +333,16 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
     }
 
     // Weights decay; the matched one gains alpha, or the last-ranked one is
-    // replaced on a miss; then renormalise.
+    // replaced on a miss; then renormalise. (Explicitly rounded operations:
+    // no multiply-add contraction, so every path rounds alike.)
     float sum = 0.f;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-        float w = c[i].w * p.oma;
+        float w = __fmul_rn(c[i].w, p.oma);
         if (i == jj)
-            w = matched ? w + p.alpha : p.init_w;
+            w = matched ? __fadd_rn(w, p.alpha) : p.init_w;
         c[i].w = w;
-        sum += w;
+        sum = __fadd_rn(sum, w);
     }
     const float inv = __fdividef(1.0f, sum); // within 2 ulp; the sum is near 1
 
@@ -378,7 +382,7 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
     // lane's components are already in non-increasing key order (the usual
     // case: a background pixel matches its best component and the others
     // decay by the same factor), the stable network would leave them as they
-    // are, so the warp skips it.
+    // are, so the warp skips it and the changed component keeps its rank.
     bool sorted = true;
 #pragma unroll
     for (int i = 1; i < M; ++i)
@@ -390,18 +394,43 @@ __device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D]
         for (int r = 0; r < M; ++r)
             if ((c[r].key & 7u) == 7u - (uint32_t)jj) // its stored rank, from the key
                 rank = r;
+        if (kJ >= 0) // (the specialised path keeps its rank known where no sort ran)
+            return background_test<M, D>(c, rank, matched, p.T);
     }
-    // Background test: the rank is in B (the shortest prefix summing past T)
-    // unless the prefix before it already sums past T (prefix sums of
-    // non-negative weights do not decrease under rounding).
-    float acc = 0.f, before = 0.f;
+    return background_test<M, D>(c, rank, matched, p.T);
+}
+
+// One tick of one mixture at one pixel (§III.A). The components are in rank
+// order on entry and on exit. Returns the stream's foreground bit.
+// kSkipSorted: let a warp skip the sorting network when it would change
+// nothing (pays where issue slots, not HBM, bound the kernel); `lanes` is
+// then the set of lanes of the warp that make this same call, computed by
+// the caller before the code diverged (unused otherwise). kFastBest (with
+// kSkipSorted): a path specialised to a match of the best-ranked component
+// when every lane of the call has one (the usual case for background
+// pixels); it computes exactly what the general path does.
+template <int M, int D, bool kSkipSorted, bool kOptions, bool kFastBest = kSkipSorted>
+__device__ __forceinline__ int mixture_step(Comp<D> (&c)[M], const float (&x)[D],
+                                            const StreamPrm &p, uint32_t lanes) {
+    // Match: first component, in rank order, within k standard deviations
+    // (bit i of hit: component i is within; the first set bit wins).
+    uint32_t hit = 0u;
+    float d2s[M];
 #pragma unroll
-    for (int r = 0; r < M - 1; ++r) {
-        acc += c[r].w;
-        if (r + 1 == rank)
-            before = acc;
+    for (int i = 0; i < M; ++i) {
+        float d2 = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < D; ++ch) {
+            const float df = x[ch] - c[i].mu[ch];
+            d2 = fmaf(df, df, d2);
+        }
+        d2s[i] = d2;
+        if (d2 < p.k2 * c[i].v)
+            hit |= 1u << i;
     }
-    return (!matched || before > p.T) ? 1 : 0;
+    if (kSkipSorted && kFastBest && __all_sync(lanes, hit & 1u))
+        return mixture_update<M, D, kSkipSorted, kOptions, 0>(c, x, p, lanes, hit, d2s);
+    return mixture_update<M, D, kSkipSorted, kOptions, -1>(c, x, p, lanes, hit, d2s);
 }
 
 // List 1 (§III.C) on the low four bits of the per-pixel byte.
@@ -488,7 +517,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
             }
             if (draw == 0u)
                 xa[3] = a[0].mu[3];
-            fg = mixture_step<M, 4, kSkipSorted, true>(a, xa, cv.pc, lanes_c);
+            fg = mixture_step<M, 4, kSkipSorted, true, (PREC != 0)>(a, xa, cv.pc, lanes_c);
         }
         void *plw = cv.planes;
 #pragma unroll
@@ -533,7 +562,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
                 d[i].mu[0] = f.mud;
                 d[i].v = f.vd;
             }
-            fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0)>(c, xc, cv.pc, lanes_c);
+            fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0), (PREC != 0)>(c, xc, cv.pc, lanes_c);
         } else {
             // The depth values stay packed (two registers per component
             // instead of three) while the colour mixture runs.
@@ -549,7 +578,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
                 dw[i] = g0.x;
                 dmv[i] = g1.y;
             }
-            fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0)>(c, xc, cv.pc, lanes_c);
+            fgc = mixture_step<M, 3, kSkipSorted, (kVariant != 0), (PREC != 0)>(c, xc, cv.pc, lanes_c);
 #pragma unroll
             for (int i = 0; i < M; ++i) {
                 d[i].w = bf16_hi(dw[i]);
@@ -575,7 +604,7 @@ __device__ __forceinline__ uint32_t process_pixel(const CamView &cv, int64_t p) 
         fb |= kDepthStarted;
         fgd = 0;
     } else {
-        fgd = mixture_step<M, 1, kSkipSorted, (kVariant != 0)>(d, xd, cv.pd, lanes_d);
+        fgd = mixture_step<M, 1, kSkipSorted, (kVariant != 0), (PREC != 0)>(d, xd, cv.pd, lanes_d);
     }
     fb = fuse_list1(fgc, fgd, fb);
 

@@ -118,11 +118,11 @@ __device__ __forceinline__ int staged_mixture_step(uint8_t *st, int f0, int t,
     float sum = 0.f;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-        float wi = w[i] * p.oma;
+        float wi = __fmul_rn(w[i], p.oma);
         if (i == jj)
-            wi = matched ? wi + p.alpha : p.init_w;
+            wi = matched ? __fadd_rn(wi, p.alpha) : p.init_w;
         w[i] = wi;
-        sum += wi;
+        sum = __fadd_rn(sum, wi);
     }
     const float inv = __fdividef(1.0f, sum);
 #pragma unroll

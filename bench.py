@@ -1457,7 +1457,7 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true",
                     help="c2: skip the extra keys (the same cameras with FP16/BF16 state, and a "
                          "short serving run)")
-    ap.add_argument("--extra-serve-seconds", type=float, default=4.0,
+    ap.add_argument("--extra-serve-seconds", type=float, default=6.0,
                     help="c2: simulated seconds of each extra serving run")
     ap.add_argument("--cpu-frames", type=int, default=21, help="oracle baseline frames (0 = skip)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle baseline rows per frame (0 = all)")

@@ -894,15 +894,18 @@ def serving_setup(G, torch, wl, rank, dev):
 
 def serving_extra(G, torch, args, dev):
     """A short run of workload c4 (256 cameras, Poisson sessions, 30 fps each,
-    80 GB budget, FP16/BF16 state) on the serving engine: frame latency
-    (arrival to fused mask in host memory), drops and rejections; the same
-    cameras as a genlocked rig (every camera's frames arrive together, so
-    each period opens with a burst that continuous batching packs into few
-    ticks); and a tight 8 GB budget, to exercise admission control."""
+    80 GB budget, FP16/BF16 state) on the serving engine in its default
+    zero-copy mode: frame latency (arrival to fused mask in host memory),
+    drops and rejections; the same cameras as a genlocked rig (every camera's
+    frames arrive together, so each period opens with a burst that continuous
+    batching packs into few ticks); a tight 8 GB budget, to exercise
+    admission control; and both schedules again in the engine's copy mode."""
     wl = WORKLOADS["c4"]
     cams, ring = serving_setup(G, torch, wl, 0, dev)
     dur = args.extra_serve_seconds
-    out = {"workload": f"c4: {wl['name']}", "duration_s": dur, "unit": "ms"}
+    out = {"workload": f"c4: {wl['name']}", "duration_s": dur, "unit": "ms",
+           "transfer": "zero-copy: the pooled kernel reads the page-locked frames and writes "
+                       "the masks in host memory"}
     st, lat, wall, _, rel_err, _, parts = serve_run(G, torch, cams, ring, wl,
                                                     int(wl["budget_gb"] * 1e9), dur, 2021)
     lat = list(lat)
@@ -928,6 +931,16 @@ def serving_extra(G, torch, args, dev):
                            "sessions_admitted": st2["admitted"],
                            "admissions_rejected": st2["rejected"],
                            "p99": fnum(pct(list(lat2), 99))}
+    # the same two schedules with the engine's copy mode (uploads, downloads)
+    cm = {}
+    for key, gl in (("independent", False), ("genlocked", True)):
+        stc, latc, _, _, _, _, _ = serve_run(G, torch, cams, ring, wl, int(wl["budget_gb"] * 1e9),
+                                             dur, 2021, genlocked=gl, transfer=G.SERVE_COPY)
+        latc = list(latc)
+        cm[key] = {"p50": fnum(pct(latc, 50)), "p99": fnum(pct(latc, 99)),
+                   "p999": fnum(pct(latc, 99.9)), "frames_completed": stc["completed"],
+                   "mean_frames_per_tick": stc["completed"] / max(stc["ticks"], 1)}
+    out["copy_mode"] = cm
     return out
 
 
@@ -1075,13 +1088,15 @@ def serving_schedule(n_cams, duration, fps, session_s, live_fraction, seed, genl
 
 
 def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_depth=4,
-              genlocked=False):
-    """Drive a Server through a seeded schedule in real time; returns stats."""
+              genlocked=False, transfer=None):
+    """Drive a Server through a seeded schedule in real time; returns stats.
+    transfer: the engine's transfer mode (None: its default, zero-copy)."""
     import queue as pyqueue
 
     import numpy as np
     srv = G.Server(budget_bytes=budget_bytes, precision=wl["prec"], max_cams=len(cams),
-                   queue_depth=queue_depth)
+                   queue_depth=queue_depth, transfer=transfer)
+    copy_mode = transfer == G.SERVE_COPY
     # device memory for every camera's state and staging mapped before the
     # clock starts (up to the budget), so no admission maps new memory
 
@@ -1089,7 +1104,7 @@ def serve_run(G, torch, cams, ring, wl, budget_bytes, duration, seed, queue_dept
         return (x + 255) // 256 * 256
     state_all = sum(G.state_bytes(H, W, M, wl["prec"]) for (H, W, M, _) in cams)
     stage_all = sum(al(H * W * 3) + al(H * W * 2) + al(H * G.mask_words_per_row(W) * 4)
-                    for (H, W, _, _) in cams)
+                    for (H, W, _, _) in cams) if copy_mode else 0
     cap = budget_bytes if budget_bytes else state_all + stage_all
     srv.reserve(min(state_all, cap), min(stage_all, max(cap - min(state_all, cap), 0)))
     events = serving_schedule(len(cams), duration, wl["fps"], wl["session_frames"] / wl["fps"],
@@ -1272,18 +1287,21 @@ def run_serving(args, wl):
     cams, ring = serving_setup(G, torch, wl, rank, dev)
     duration = args.serve_seconds or wl["duration_s"]
     barrier(world, dev)
+    transfer = G.SERVE_COPY if args.serve_copy else G.SERVE_ZERO_COPY
     st, lat, wall, lag, rel_err, admit_ms, parts = serve_run(G, torch, cams, ring, wl,
-                                            int(wl["budget_gb"] * 1e9), duration, 2021 + rank)
+                                            int(wl["budget_gb"] * 1e9), duration, 2021 + rank,
+                                            transfer=transfer)
     wall = reduce_max(wall, world, dev)
     pixels = st["pixels"]
     total_px = pixels * world  # weak scaling: every rank serves its own cameras
     value = total_px / wall / 1e6
     st2, lat2, _, _, _, _, _ = serve_run(G, torch, cams, ring, wl, int(wl["tight_budget_gb"] * 1e9),
-                                   wl["tight_duration_s"], 77 + rank)
+                                   wl["tight_duration_s"], 77 + rank, transfer=transfer)
     # a genlocked rig: the cameras live at the start deliver their frames
     # together every period, so each period opens with one large burst
     st3, lat3, _, _, _, _, parts3 = serve_run(G, torch, cams, ring, wl, int(wl["budget_gb"] * 1e9),
-                                              wl["tight_duration_s"], 2021 + rank, genlocked=True)
+                                              wl["tight_duration_s"], 2021 + rank, genlocked=True,
+                                              transfer=transfer)
     ev3 = serving_schedule(len(cams), wl["tight_duration_s"], wl["fps"],
                            wl["session_frames"] / wl["fps"], wl["live_fraction"], 2021 + rank, True)
     burst_px = sum(cams[c][0] * cams[c][1] for (t, kind, c, _) in ev3 if t == 0.0 and kind == 0)
@@ -1307,7 +1325,8 @@ def run_serving(args, wl):
                            "max": float(lat[-1]) if lat.size else None,
                            "what": "frame arrival to fused mask in host memory",
                            "breakdown": parts},
-            "serving": {"frames_completed": st["completed"], "frames_dropped": st["dropped"],
+            "serving": {"transfer": "copy" if args.serve_copy else "zero-copy",
+                        "frames_completed": st["completed"], "frames_dropped": st["dropped"],
                         "sessions_admitted": st["admitted"], "admissions_rejected": st["rejected"],
                         "ticks": st["ticks"], "mean_frames_per_tick": st["completed"] / max(st["ticks"], 1),
                         "driver_lag_ms_p99": fnum(pct(lag, 99)),
@@ -1442,6 +1461,8 @@ def main(argv=None):
     ap.add_argument("--no-graph", action="store_true", help="pooled workloads: no CUDA graph")
     ap.add_argument("--serve-seconds", type=float, default=0.0,
                     help="serving workload: simulated seconds (0: the workload's 20)")
+    ap.add_argument("--serve-copy", action="store_true",
+                    help="serving workload: the engine's copy mode instead of zero-copy")
     ap.add_argument("--no-autotune", action="store_true", help="pooled workloads: default launch")
     ap.add_argument("--pool-launch", default="",
                     help="pooled workloads: THREADS,CTAS_PER_SM,TILE_PIXELS instead of tuning "

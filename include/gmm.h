@@ -463,12 +463,23 @@ int gmm_pool_destroy(gmm_pool_t *p);
  * paper's per-sensor frame stream, §IV, Fig. 4(a), for several sensors as in
  * §VI), served with continuous batching: an engine thread repeatedly forms a
  * tick from every camera that has a queued frame and no frame in flight,
- * uploads those frames, advances them together with one pooled launch,
- * downloads their masks, and records each frame's latency from its arrival
- * time to its mask being in host memory. Frames that arrive while a tick is
- * on the GPU join a later tick; uploads, compute and downloads of
- * consecutive ticks overlap on separate streams. Each camera's model stays
- * resident in device memory between its frames. */
+ * advances those frames together with one pooled launch, and records each
+ * frame's latency from its arrival time to its mask being in host memory.
+ * Frames that arrive while a tick is on the GPU join a later tick, which is
+ * queued behind it at once. Each camera's model stays resident in device
+ * memory between its frames.
+ *
+ * Transfer modes (gmm_server_set_transfer):
+ *   GMM_SERVE_ZERO_COPY (default): the pooled kernel reads each frame and
+ *     writes each mask in the caller's page-locked host memory directly,
+ *     over the coherent host link; no copies and no per-camera device
+ *     buffers.
+ *   GMM_SERVE_COPY: the engine uploads each frame into a per-camera device
+ *     buffer and downloads the mask (Fig. 4(a)'s three-stage pipeline), the
+ *     uploads, compute and downloads of consecutive ticks overlapping on
+ *     separate streams. */
+#define GMM_SERVE_ZERO_COPY 0
+#define GMM_SERVE_COPY 1
 typedef struct gmm_server gmm_server_t;
 
 typedef struct gmm_server_stats {
@@ -477,7 +488,7 @@ typedef struct gmm_server_stats {
     long long ticks;                      /* pooled launches */
     long long pixels;                     /* pixels of completed frames */
     int live_cams;
-    size_t budget_bytes, used_bytes;      /* state + staging of admitted cameras */
+    size_t budget_bytes, used_bytes;      /* state (+ staging, copy mode) of admitted cameras */
     double max_engine_gap_ms;             /* longest time between two passes of the
                                              engine's loop (a pass waits at most
                                              0.2 ms for work; a longer gap means the
@@ -485,12 +496,17 @@ typedef struct gmm_server_stats {
                                              lock, or not scheduled) */
 } gmm_server_stats;
 
-/* budget_bytes caps the device memory of admitted cameras (state plus the
- * per-camera upload and mask buffers; 0 = no cap). max_cams: slots.
+/* budget_bytes caps the device memory of admitted cameras (state, plus in
+ * the copy mode the per-camera upload and mask buffers; 0 = no cap).
+ * max_cams: slots.
  * queue_depth: frames a camera may have waiting (>= 1). Starts the engine
  * thread on the current device. NULL on error. */
 gmm_server_t *gmm_server_create(size_t budget_bytes, int precision, int max_cams,
                                 int queue_depth);
+
+/* Choose the transfer mode (GMM_SERVE_ZERO_COPY or GMM_SERVE_COPY) before the
+ * first admission; GMM_EINVAL afterwards or for another value. */
+int gmm_server_set_transfer(gmm_server_t *s, int mode);
 
 /* Admit a camera (cfg->precision must equal the server's). Returns its id,
  * or GMM_EBUDGET when its memory would exceed the budget (the admission is
@@ -498,7 +514,8 @@ gmm_server_t *gmm_server_create(size_t budget_bytes, int precision, int max_cams
 int gmm_server_admit(gmm_server_t *s, const gmm_config *cfg);
 
 /* As gmm_pool_reserve for the server: state_bytes for camera state,
- * staging_bytes for the per-camera upload and mask buffers; same statuses.
+ * staging_bytes for the per-camera upload and mask buffers of the copy mode
+ * (0 in the zero-copy mode); same statuses.
  * May be called from any thread; synchronous: it waits for the work queued
  * on the engine's compute stream, so call it before the frames flow. */
 int gmm_server_reserve(gmm_server_t *s, size_t state_bytes, size_t staging_bytes);
@@ -507,12 +524,14 @@ int gmm_server_reserve(gmm_server_t *s, size_t state_bytes, size_t staging_bytes
  * its queued frames are done, then frees its slot and memory. */
 int gmm_server_release(gmm_server_t *s, int cam, int timeout_ms);
 
-/* Queue one frame. rgb8_host, depth16_host: host, page-locked for
- * overlapped copies, read when the frame's tick is formed; mask_host: host,
- * receives the fused mask. All three must stay valid until the frame is
- * done. t_arrival: arrival time on the gmm_server_now() clock. Returns a
- * ticket >= 0, or GMM_EBUDGET if the camera's queue is full (the frame is
- * dropped and counted), or another negative status. */
+/* Queue one frame. rgb8_host, depth16_host: host memory, page-locked (in
+ * the zero-copy mode the device must be able to reach it, else GMM_EINVAL;
+ * in the copy mode page-locked memory lets the uploads overlap), read when
+ * the frame's tick runs; mask_host: host, receives the fused mask. All three
+ * must stay valid and unmodified until the frame is done. t_arrival: arrival
+ * time on the gmm_server_now() clock. Returns a ticket >= 0, or GMM_EBUDGET if
+ * the camera's queue is full (the frame is dropped and counted), or another
+ * negative status. */
 long long gmm_server_push(gmm_server_t *s, int cam, const uint8_t *rgb8_host,
                           const uint16_t *depth16_host, uint32_t *mask_host,
                           double t_arrival);
@@ -532,9 +551,10 @@ size_t gmm_server_latencies(gmm_server_t *s, float *ms_out, size_t n);
 
 /* Where a completed frame's latency went, on the gmm_server_now() clock
  * (seconds): t_arrival as given to gmm_server_push; t_pushed when that call
- * queued it; t_batched when the engine took the frame into a tick; t_submitted when that tick's uploads, launch and downloads
- * were queued on the device; t_done when the engine saw the tick's last
- * download complete (the latency's end). cam: the server's camera id;
+ * queued it; t_batched when the engine took the frame into a tick;
+ * t_submitted when that tick's launch (and copies, in the copy mode) were
+ * queued on the device; t_done when the engine saw the tick complete, its
+ * masks in host memory (the latency's end). cam: the server's camera id;
  * tick_frames: frames in the same tick. */
 typedef struct gmm_server_trace {
     long long ticket;

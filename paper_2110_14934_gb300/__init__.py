@@ -19,7 +19,8 @@ from . import _build
 __all__ = ["GMM", "Pool", "GMMError", "fuse_masks", "morph_open3", "mask_words_per_row",
            "state_bytes", "unpack_mask", "pack_mask", "load_library", "PLANES",
            "PREC_F32", "PREC_F16", "make_config", "MODE_FUSION", "MODE_AUGMENTED",
-           "FLAG_RHO_ETA", "FLAG_VAR_PER_CHANNEL", "FLAG_STOCHASTIC_WEIGHTS"]
+           "FLAG_RHO_ETA", "FLAG_VAR_PER_CHANNEL", "FLAG_STOCHASTIC_WEIGHTS", "Server",
+           "SERVE_ZERO_COPY", "SERVE_COPY"]
 
 OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT = 0, -1, -2, -3, -4, -5
 PLANE_W_C, PLANE_MU_R, PLANE_MU_G, PLANE_MU_B, PLANE_V_C, PLANE_W_D, PLANE_MU_D, PLANE_V_D, \
@@ -30,6 +31,7 @@ PIPE_DEPTH = 3
 KERNEL_STAGED, KERNEL_DIRECT = 0, 1
 MODE_FUSION, MODE_AUGMENTED = 0, 1
 FLAG_RHO_ETA, FLAG_VAR_PER_CHANNEL, FLAG_STOCHASTIC_WEIGHTS = 1, 2, 4
+SERVE_ZERO_COPY, SERVE_COPY = 0, 1
 
 _ERRNAMES = {EINVAL: "GMM_EINVAL", ENOMEM: "GMM_ENOMEM", ECUDA: "GMM_ECUDA",
              EBUDGET: "GMM_EBUDGET", ETIMEOUT: "GMM_ETIMEOUT"}
@@ -131,6 +133,7 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_pool_destroy": (ctypes.c_int, [_vp]),
         "gmm_server_create": (_vp, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "gmm_server_admit": (ctypes.c_int, [_vp, ctypes.POINTER(GMMConfig)]),
+        "gmm_server_set_transfer": (ctypes.c_int, [_vp, ctypes.c_int]),
         "gmm_server_release": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
         "gmm_server_push": (ctypes.c_longlong, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double]),
         "gmm_server_done": (ctypes.c_int, [_vp, ctypes.c_longlong]),
@@ -450,10 +453,12 @@ class Pool:
 
 class Server:
     """Continuous-batching serving engine: cameras join and leave, frames
-    arrive in page-locked host memory, one pooled launch per tick."""
+    arrive in page-locked host memory, one pooled launch per tick.
+    transfer: SERVE_ZERO_COPY (the kernel reads frames and writes masks in
+    host memory) or SERVE_COPY (uploads and downloads on copy streams)."""
 
     def __init__(self, budget_bytes=0, precision=PREC_F16, max_cams=256, queue_depth=4,
-                 device=None):
+                 device=None, transfer=None):
         import torch
         L = load_library()
         self.device = torch.device("cuda" if device is None else device)
@@ -464,6 +469,8 @@ class Server:
             raise GMMError(EINVAL, _err())
         self._s = s
         self.cams = {}
+        if transfer is not None:
+            _check(L.gmm_server_set_transfer(s, transfer))
 
     @staticmethod
     def now() -> float:

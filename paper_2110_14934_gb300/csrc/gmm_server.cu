@@ -1,9 +1,12 @@
 // Serving engine: continuous batching of frames from many cameras over the
 // multi-camera pool. Client threads admit cameras and push frames that live
-// in page-locked host memory; one engine thread forms ticks, uploads the
-// frames, launches the pooled kernel, downloads the masks and stamps
-// latencies. Uploads, compute and downloads run on three streams, so the
-// copies of one tick overlap the compute of its neighbours.
+// in page-locked host memory; one engine thread forms ticks, launches the
+// pooled kernel and stamps latencies. By default the pooled kernel reads
+// the frames and writes the masks in that host memory directly (over the
+// coherent host link: no copies, no staging buffers); in the copy mode the
+// engine uploads the frames into per-camera device buffers and downloads the
+// masks, on separate streams so the copies of one tick overlap the compute
+// of its neighbours.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,6 +67,7 @@ struct TickRec {
 
 struct gmm_server {
     int device = 0, prec = 0, queue_depth = 1;
+    int transfer = GMM_SERVE_ZERO_COPY; // fixed once a camera has been admitted
     size_t budget = 0, used = 0;
     gmm_pool_t *pool = nullptr;
     std::vector<SrvCam> cams;
@@ -152,6 +156,21 @@ static void harvest(gmm_server *s, bool block) {
 static cudaError_t enqueue_tick(gmm_server *s, TickRec &t) {
     TraceRange tr("gmm_server tick");
     cudaError_t e = cudaSuccess;
+    if (s->transfer == GMM_SERVE_ZERO_COPY) {
+        // the kernel reads the frames and writes the masks in host memory
+        {
+            std::lock_guard<std::mutex> lk(s->pool_mu);
+            for (auto &j : t.jobs) {
+                SrvCam &c = s->cams[j.first];
+                if (gmm_pool_submit(s->pool, c.pool_id, j.second.rgb, j.second.depth,
+                                    j.second.mask, nullptr, nullptr) != GMM_OK)
+                    return cudaErrorInvalidValue;
+            }
+            if (gmm_pool_tick(s->pool) != GMM_OK)
+                return cudaErrorLaunchFailure;
+        }
+        return cudaEventRecord(t.done, s->s_comp);
+    }
     for (auto &j : t.jobs) {
         SrvCam &c = s->cams[j.first];
         if (e == cudaSuccess)
@@ -313,6 +332,18 @@ gmm_server_t *gmm_server_create(size_t budget_bytes, int precision, int max_cams
     return s;
 }
 
+int gmm_server_set_transfer(gmm_server_t *s, int mode) {
+    if (!s)
+        return fail(GMM_EINVAL, "gmm_server_set_transfer: null server");
+    if (mode != GMM_SERVE_ZERO_COPY && mode != GMM_SERVE_COPY)
+        return fail(GMM_EINVAL, "gmm_server_set_transfer: unknown mode");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->st.admitted > 0)
+        return fail(GMM_EINVAL, "gmm_server_set_transfer: set it before the first admission");
+    s->transfer = mode;
+    return GMM_OK;
+}
+
 int gmm_server_admit(gmm_server_t *s, const gmm_config *cfg) {
     if (!s)
         return fail(GMM_EINVAL, "gmm_server_admit: null server");
@@ -324,7 +355,8 @@ int gmm_server_admit(gmm_server_t *s, const gmm_config *cfg) {
     const size_t wpr = (size_t)(cfg->W + 31) / 32;
     const size_t rgb = (size_t)cfg->H * cfg->W * 3, dep = (size_t)cfg->H * cfg->W * 2;
     const size_t msk = (size_t)cfg->H * wpr * 4;
-    const size_t staging = align256(rgb) + align256(dep) + align256(msk);
+    const size_t staging =
+        s->transfer == GMM_SERVE_COPY ? align256(rgb) + align256(dep) + align256(msk) : 0;
     const size_t bytes = gmm_state_bytes(cfg->H, cfg->W, cfg->M, cfg->precision) + staging;
     int slot = -1;
     {
@@ -352,7 +384,7 @@ int gmm_server_admit(gmm_server_t *s, const gmm_config *cfg) {
         std::lock_guard<std::mutex> lk(s->pool_mu);
         pid = gmm_pool_admit(s->pool, cfg);
         cudaError_t e = cudaSuccess;
-        if (pid >= 0) {
+        if (pid >= 0 && staging > 0) {
             e = cudaMallocFromPoolAsync(&buf, staging, s->mempool, s->s_comp);
             if (e == cudaSuccess)
                 e = cudaEventRecord(s->ev_alloc, s->s_comp);
@@ -425,7 +457,8 @@ int gmm_server_release(gmm_server_t *s, int cam, int timeout_ms) {
     {
         std::lock_guard<std::mutex> plk(s->pool_mu);
         gmm_pool_release(s->pool, c.pool_id);
-        e = cudaFreeAsync(c.d_buf, s->s_comp); // after any queued use on the stream
+        e = c.d_buf ? cudaFreeAsync(c.d_buf, s->s_comp) // after any queued use on the stream
+                    : cudaSuccess;
     }
     lk.lock();
     s->cams[cam] = SrvCam();
@@ -451,6 +484,13 @@ long long gmm_server_push(gmm_server_t *s, int cam, const uint8_t *rgb8_host,
     if (cam < 0 || cam >= (int)s->cams.size() || !s->cams[cam].used)
         return fail(GMM_EINVAL, "gmm_server_push: unknown camera");
     SrvCam &c = s->cams[cam];
+    if (s->transfer == GMM_SERVE_ZERO_COPY) { // the kernel will read and write them itself
+        const std::string msg = check_frame_ptrs(rgb8_host, depth16_host, mask_host, nullptr,
+                                                 nullptr);
+        if (!msg.empty())
+            return fail(GMM_EINVAL, "gmm_server_push (zero-copy mode: page-locked host memory the "
+                                    "device can reach, or GMM_SERVE_COPY): " + msg);
+    }
     if ((int)c.queue.size() >= s->queue_depth) {
         s->st.dropped += 1;
         return fail(GMM_EBUDGET, "gmm_server_push: camera queue full, frame dropped");

@@ -140,6 +140,7 @@ def test_server_host_checks():
     assert L.gmm_server_wait(None, 0, 0) == G.EINVAL
     assert L.gmm_server_destroy(None, 0) == G.EINVAL
     assert L.gmm_server_reserve(None, 0, 0) == G.EINVAL
+    assert L.gmm_server_set_transfer(None, G.SERVE_COPY) == G.EINVAL
     assert L.gmm_pool_reserve(None, 0) == G.EINVAL
     t0 = L.gmm_server_now()
     t1 = L.gmm_server_now()

@@ -24,8 +24,12 @@ def _pinned(frames):
     return r, d
 
 
+TRANSFER = [pytest.param(G.SERVE_ZERO_COPY, id="zero_copy"), pytest.param(G.SERVE_COPY, id="copy")]
+
+
+@pytest.mark.parametrize("transfer", TRANSFER)
 @pytest.mark.parametrize("prec", [G.PREC_F16, G.PREC_F32])
-def test_server_results_equal_alone_in_a_changing_mix(prec):
+def test_server_results_equal_alone_in_a_changing_mix(prec, transfer):
     import torch
     n = 10
     frames = [scene_frames(700 + i, H, W, 1, 40, n) for i, (H, W, M) in enumerate(CAMS)]
@@ -35,7 +39,7 @@ def test_server_results_equal_alone_in_a_changing_mix(prec):
         for t in range(n):
             r, d = to_dev(frames[i][0][t], frames[i][1][t])
             alone[(i, t)] = words(g.apply(r, d)).copy()
-    srv = G.Server(precision=prec, max_cams=8, queue_depth=n)
+    srv = G.Server(precision=prec, max_cams=8, queue_depth=n, transfer=transfer)
     ids = [srv.admit(H, W, M) for (H, W, M) in CAMS]
     pinned = [_pinned(f) for f in frames]
     masks = {(i, t): torch.zeros((H, G.mask_words_per_row(W)), dtype=torch.int32).pin_memory()
@@ -74,9 +78,11 @@ def test_server_results_equal_alone_in_a_changing_mix(prec):
     srv.close()
 
 
-def test_server_budget_admission_and_release():
+@pytest.mark.parametrize("transfer", TRANSFER)
+def test_server_budget_admission_and_release(transfer):
     per = G.state_bytes(120, 160, 5, G.PREC_F16)
-    srv = G.Server(budget_bytes=int(2.5 * per) + 400000, precision=G.PREC_F16, max_cams=4)
+    srv = G.Server(budget_bytes=int(2.5 * per) + 400000, precision=G.PREC_F16, max_cams=4,
+                   transfer=transfer)
     a = srv.admit(120, 160, 5)
     b = srv.admit(120, 160, 5)
     with pytest.raises(G.GMMError) as e:
@@ -94,11 +100,12 @@ def test_server_budget_admission_and_release():
     srv.close()
 
 
-def test_server_full_queue_drops_frames():
+@pytest.mark.parametrize("transfer", TRANSFER)
+def test_server_full_queue_drops_frames(transfer):
     import torch
     H, W, M = 720, 1280, 5
     rgb, depth = _pinned(scene_frames(3, H, W, 1, 0, 2))
-    srv = G.Server(precision=G.PREC_F16, max_cams=2, queue_depth=1)
+    srv = G.Server(precision=G.PREC_F16, max_cams=2, queue_depth=1, transfer=transfer)
     cam = srv.admit(H, W, M)
     mask = torch.zeros((H, G.mask_words_per_row(W)), dtype=torch.int32).pin_memory()
     tickets, drops = [], 0
@@ -114,4 +121,32 @@ def test_server_full_queue_drops_frames():
     assert drops >= 1 and st["dropped"] == drops
     assert st["pushed"] == len(tickets) and st["completed"] == len(tickets)
     srv.release(cam, 10000)
+    srv.close()
+
+
+def test_server_transfer_mode_rules():
+    """The mode is fixed once a camera is admitted; the zero-copy mode takes
+    only host memory the device can reach (pageable memory is refused at
+    push, with no frame queued), while the copy mode uploads from it."""
+    import torch
+    H, W, M = 48, 64, 3
+    rgb, depth, _ = scene_frames(9, H, W, 1, 0, 1)
+    srv = G.Server(precision=G.PREC_F16, max_cams=2)
+    cam = srv.admit(H, W, M)
+    with pytest.raises(G.GMMError) as e:
+        G._check(G.load_library().gmm_server_set_transfer(srv._s, G.SERVE_COPY))
+    assert e.value.code == G.EINVAL
+    pageable_mask = np.zeros((H, G.mask_words_per_row(W)), np.uint32)
+    with pytest.raises(G.GMMError) as e:
+        srv.push(cam, np.ascontiguousarray(rgb[0]), np.ascontiguousarray(depth[0]), pageable_mask)
+    assert e.value.code == G.EINVAL and srv.stats()["pushed"] == 0
+    srv.close()
+    srv = G.Server(precision=G.PREC_F16, max_cams=2, transfer=G.SERVE_COPY)
+    cam = srv.admit(H, W, M)
+    want = G.GMM(H, W, M, precision=G.PREC_F16)
+    r, d = to_dev(rgb[0], depth[0])
+    ref = words(want.apply(r, d))
+    srv.wait(srv.push(cam, np.ascontiguousarray(rgb[0]), np.ascontiguousarray(depth[0]),
+                      pageable_mask), 30000)
+    assert np.array_equal(pageable_mask, ref)
     srv.close()

@@ -65,6 +65,9 @@ KERNELS = {"staged": 0, "direct": 1}
 METRIC = "Mpixel-frames/s (RGB+depth GMM+fusion)"
 UNIT = "Mpixel-frames/s"
 FALLBACK_HBM_GBS = 6800.0
+# end-to-end passes take at least this many steps (fewer would mostly time the
+# pipeline filling and draining)
+E2E_MIN_STEPS = 200
 L2_BYTES = 129 * 1024 * 1024
 CSRC = os.path.join(ROOT, "paper_2110_14934_gb300", "csrc")
 # Committed ncu captures whose DRAM traffic the roofline quotes, keyed by
@@ -554,7 +557,7 @@ def run_gmm(args, wl):
 
     # end to end through the host-memory C-ABI path (pipelined, Fig. 4(a))
     e2e = run_e2e(G, torch, g_args=(H, W, M, prec), frames=(rgb_d, dep_d), dev=dev,
-                  steps=args.e2e_steps or K, warmup=Wm, world=world,
+                  steps=args.e2e_steps or max(K, E2E_MIN_STEPS), warmup=Wm, world=world,
                   kernel=(KERNELS[args.kernel], args.variant, args.ctas), morph=args.morph)
     del rgb_d, dep_d
     cpu = None
@@ -747,7 +750,7 @@ def run_pool(args, wl):
     for g in plain:
         g.set_stream(stream)
     hs = [g._h for g in plain]
-    n_plain = min(K, 300)
+    n_plain = min(max(K, 100), 300)  # at least 100 ticks: a steady comparison
     for k in range(Wm):
         for i, h in enumerate(hs):
             L.gmm_apply(h, rgb_base[i] + (k % nf) * rgb_step[i], dep_base[i] + (k % nf) * dep_step[i],
@@ -766,7 +769,8 @@ def run_pool(args, wl):
     for g in plain:
         g.close()
 
-    e2e = run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, args.e2e_steps or min(K, 600),
+    e2e = run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream,
+                       args.e2e_steps or min(max(K, E2E_MIN_STEPS), 600),
                        Wm, world)
     # c2 at N = 1: the same cameras and frames with FP16/BF16 state (the
     # precision configuration) and a short run of the serving engine
@@ -1450,7 +1454,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gmm", "reference"], default="gmm")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
-    ap.add_argument("--e2e-steps", type=int, default=0, help="0: same as --steps")
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="0: --steps, at least 200 (pooled workloads: at most 600)")
     ap.add_argument("--kernel", choices=sorted(KERNELS), default="direct")
     ap.add_argument("--variant", type=int, default=0, help="staged tile shape 0-3")
     ap.add_argument("--ctas", type=int, default=0, help="staged CTAs per SM (0: as many as fit)")

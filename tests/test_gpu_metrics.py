@@ -14,7 +14,7 @@ from parity import to_dev
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("H,W", [(1, 1), (3, 33), (64, 96), (37, 1000), (480, 640)])
+@pytest.mark.parametrize("H,W", [(1, 1), (3, 33), (64, 96), (37, 1000), (480, 640), (1080, 1920)])
 def test_pack_and_confusion_counts(H, W):
     import torch
     rng = np.random.default_rng(H * 7 + W)

@@ -43,6 +43,31 @@ def test_fuse_masks_exhaustive_sequences():
         assert np.array_equal(fb & 1, Fo) and np.array_equal(((fb >> 1) & 7) - 3, co), t
 
 
+def test_fuse_masks_matches_the_tick_at_full_size():
+    """At 1920x1080, gmm_fuse_masks applied to a tick's colour and depth
+    masks and the List-1 bytes from before the tick gives the tick's fused
+    mask and List-1 state (label and counter, the low four bits) exactly: the
+    operator and the fused kernel run the same List 1. (Bit 4, the depth
+    model's start, belongs to the tick, not to List 1.)"""
+    import torch
+    H, W, M = 1080, 1920, 5
+    s = synth.scene(606, H, W, 1)
+    rgb, dep, _ = synth.frames_device(s, 40, 4, with_gt=False)
+    g = G.GMM(H, W, M)
+    out = g.new_mask()
+    for t in range(4):
+        before = torch.from_numpy(g.fusion()).cuda()
+        m, fc, fd = g.new_mask(), g.new_mask(), g.new_mask()
+        g.apply(rgb[t], dep[t], m, fc, fd)
+        torch.cuda.synchronize()
+        if t == 0:
+            continue  # the first tick initialises the models
+        G.fuse_masks(fc, fd, before, out, H, W)
+        torch.cuda.synchronize()
+        assert torch.equal(out, m), t
+        assert np.array_equal(before.cpu().numpy() & 15, g.fusion() & 15), t
+
+
 @pytest.mark.parametrize("H,W", [(1, 1), (1, 40), (5, 1), (9, 13), (33, 65), (100, 1000)])
 def test_morph_open3_matches_oracle(H, W):
     import torch

@@ -67,7 +67,7 @@ struct TickRec {
 
 struct gmm_server {
     int device = 0, prec = 0, queue_depth = 1;
-    int transfer = GMM_SERVE_ZERO_COPY; // fixed once a camera has been admitted
+    std::atomic<int> transfer{GMM_SERVE_ZERO_COPY}; // fixed once a camera has been admitted
     size_t budget = 0, used = 0;
     gmm_pool_t *pool = nullptr;
     std::vector<SrvCam> cams;
@@ -477,13 +477,6 @@ long long gmm_server_push(gmm_server_t *s, int cam, const uint8_t *rgb8_host,
         return fail(GMM_EINVAL, "gmm_server_push: null server");
     if (!rgb8_host || !depth16_host || !mask_host)
         return fail(GMM_EINVAL, "gmm_server_push: null buffer");
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->sticky != cudaSuccess)
-        return fail(GMM_ECUDA, std::string("gmm_server_push: earlier CUDA failure: ") +
-                                   cudaGetErrorString(s->sticky));
-    if (cam < 0 || cam >= (int)s->cams.size() || !s->cams[cam].used)
-        return fail(GMM_EINVAL, "gmm_server_push: unknown camera");
-    SrvCam &c = s->cams[cam];
     if (s->transfer == GMM_SERVE_ZERO_COPY) { // the kernel will read and write them itself
         const std::string msg = check_frame_ptrs(rgb8_host, depth16_host, mask_host, nullptr,
                                                  nullptr);
@@ -491,6 +484,13 @@ long long gmm_server_push(gmm_server_t *s, int cam, const uint8_t *rgb8_host,
             return fail(GMM_EINVAL, "gmm_server_push (zero-copy mode: page-locked host memory the "
                                     "device can reach, or GMM_SERVE_COPY): " + msg);
     }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->sticky != cudaSuccess)
+        return fail(GMM_ECUDA, std::string("gmm_server_push: earlier CUDA failure: ") +
+                                   cudaGetErrorString(s->sticky));
+    if (cam < 0 || cam >= (int)s->cams.size() || !s->cams[cam].used)
+        return fail(GMM_EINVAL, "gmm_server_push: unknown camera");
+    SrvCam &c = s->cams[cam];
     if ((int)c.queue.size() >= s->queue_depth) {
         s->st.dropped += 1;
         return fail(GMM_EBUDGET, "gmm_server_push: camera queue full, frame dropped");

@@ -1510,6 +1510,10 @@ def main(argv=None):
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     wl = dict(WORKLOADS[args.workload])
+    multi = wl.get("pool") or wl.get("serve")
+    if multi and (args.morph or args.frame_size or args.kernel != "direct"):
+        ap.error("--morph, --frame-size and --kernel apply to the single-camera workloads "
+                 "(--workload c0 or c1)")
     if args.precision != "default":
         wl["prec"] = 0 if args.precision == "f32" else 1
         wl["name"] += f" [state overridden: {args.precision}]"

@@ -413,15 +413,18 @@ int gmm_pool_autotune(gmm_pool_t *p, int iters, int *threads,
 /* Online tuning of the launch shape on real ticks: the next
  * ticks_per_shape x (number of candidates) calls of gmm_pool_tick each run
  * one candidate shape (block size 64/128/256; the persistent form at full or
- * half residency with tiles of 512/1024/2048/8192 pixels; round-robin, CUDA
+ * half residency with tiles of 256/512/1024/2048/8192 pixels; round-robin, CUDA
  * graphs off meanwhile; the flat form is chosen only explicitly). Each such tick is timed on the
  * pool's stream from its start to the start of the next tick (the tick
  * period, so whatever the tick's kernel delays among the work queued before
  * the next tick, such as uploads of the next frames, counts against its
- * shape). One tick after the last trial, once all have completed, the shape
- * with the lowest median period is kept and graph use restored. The ticks do
- * their normal work, so nothing is snapshotted. gmm_pool_set_launch during
- * tuning is overridden. */
+ * shape). Once every trial has completed, the 4 shapes with the lowest median
+ * periods run a second round of 2 x ticks_per_shape ticks each (ticks
+ * between the rounds, until the first round's timings are read, keep the
+ * last trial's shape), and the one with the lowest median period in that
+ * round is kept and graph use restored. The ticks do their
+ * normal work, so nothing is snapshotted. gmm_pool_set_launch during tuning
+ * is overridden. */
 int gmm_pool_autotune_online(gmm_pool_t *p, int ticks_per_shape);
 
 /* Polls online tuning (non-blocking). Returns 1 while it is still running,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 #include <cstring>
 #include <new>
 #include <string>
@@ -57,15 +58,20 @@ int chunk_pixels(int prec) { return prec == 0 ? 32 : 64; }
 // tick is timed on the pool's stream from its start to the start of the
 // next tick (the tick period), so a shape is also charged for what its
 // kernel delays in the work queued before the next tick (uploads of the next
-// frames sharing HBM with it, in a pipeline). When every candidate has run
-// its ticks, the shape with the lowest median period is kept.
+// frames sharing HBM with it, in a pipeline). Two rounds: when every
+// candidate has run its ticks, the kFinalists shapes with the lowest median
+// periods run again with twice the ticks each, and the lowest median of
+// that second round is kept (shapes a few percent apart are told apart
+// without giving every candidate the longer run).
 struct Trial {
     int cand = -1;
     cudaEvent_t a = nullptr, b = nullptr;
 };
+constexpr int kFinalists = 4;
 struct Tuning {
     bool active = false;
     bool saved_graph = false;
+    bool final_round = false;
     int per_shape = 0, issued = 0;
     std::vector<Shape> cands;
     Trial open;                 // the last trial tick, until the next tick starts
@@ -140,7 +146,7 @@ static int blocks_for(gmm_pool *p) {
 static std::vector<Shape> tuning_candidates(const gmm_pool *p) {
     std::vector<Shape> out;
     const int cand_threads[] = {64, 128, 256};
-    const int cand_tiles[] = {512, 1024, 2048, 8192};
+    const int cand_tiles[] = {256, 512, 1024, 2048, 8192};
     for (int t : cand_threads) {
         const int max_c = gmmhost::pool_max_ctas_per_sm(p->prec, t);
         const int cand_c[2] = {max_c, max_c > 1 ? max_c / 2 : 0};
@@ -185,15 +191,27 @@ static int tuning_poll(gmm_pool *p, bool block) {
     const int total = (int)tu.cands.size() * tu.per_shape;
     if (tu.issued < total || tu.open.a || !tu.pending.empty())
         return GMM_OK;
-    int best = 0;
-    float best_ms = -1.f;
+    std::vector<std::pair<float, int>> order; // (median period, candidate); untimed last
     for (size_t c = 0; c < tu.cands.size(); ++c) {
         const float m = median(tu.ms[c]);
-        if (m >= 0.f && (best_ms < 0.f || m < best_ms)) {
-            best_ms = m;
-            best = (int)c;
-        }
+        order.push_back({m >= 0.f ? m : 3.4e38f, (int)c});
     }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<float, int> &x, const std::pair<float, int> &y) {
+                         return x.first < y.first;
+                     });
+    if (!tu.final_round && (int)tu.cands.size() > kFinalists) {
+        std::vector<Shape> fin;
+        for (int i = 0; i < kFinalists; ++i)
+            fin.push_back(tu.cands[order[i].second]);
+        tu.cands = fin;
+        tu.ms.assign(fin.size(), {});
+        tu.per_shape *= 2;
+        tu.issued = 0;
+        tu.final_round = true;
+        return GMM_OK; // the next ticks run the finalists
+    }
+    const int best = order[0].second;
     p->threads = tu.cands[best].threads;
     p->ctas_per_sm = tu.cands[best].ctas;
     p->tile_pixels = tu.cands[best].tile;
@@ -612,6 +630,7 @@ int gmm_pool_autotune_online(gmm_pool_t *p, int ticks_per_shape) {
     tu.ms.assign(tu.cands.size(), {});
     tu.per_shape = ticks_per_shape;
     tu.issued = 0;
+    tu.final_round = false;
     tu.saved_graph = p->use_graph;
     p->use_graph = false; // each trial tick launches directly
     tu.active = true;

@@ -190,10 +190,11 @@ def test_pool_autotune_leaves_state_unchanged():
 
 
 def test_pool_online_tuning_changes_nothing_but_speed():
-    """Online tuning runs real ticks under every candidate launch shape (24
-    of them, one tick each here, graphs requested): the results still equal
-    each camera run alone, tuning finishes, and graph use resumes."""
-    n = 28
+    """Online tuning runs real ticks under every candidate launch shape (30
+    of them, one tick each here, then 4 finalists two ticks each; graphs
+    requested): the results still equal each camera run alone, tuning
+    finishes, and graph use resumes."""
+    n = 50
     frames = _frames(n)
     schedule = [set(range(len(CAMS)))] * n
     a = _alone(frames, schedule)

@@ -786,7 +786,7 @@ def run_pool(args, wl):
 
     e2e = run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream,
                        args.e2e_steps or min(max(K, E2E_MIN_STEPS), 600),
-                       Wm, world)
+                       Wm, world, retune=not args.pool_launch and not args.no_autotune)
     # c2 at N = 1: the same cameras and frames with FP16/BF16 state (the
     # precision configuration) and a short run of the serving engine
     extras = args.workload == "c2" and world == 1 and not args.no_extras
@@ -814,9 +814,12 @@ def run_pool(args, wl):
             "e2e": {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
                     "d2h_bytes_per_step": e2e["d2h"], "launch": e2e["launch"],
                     "path": "pinned packed tick-sets -> device staging (copy stream) -> "
-                            "gmm_pool_submit_many + gmm_pool_tick -> masks to pinned host"},
+                            "gmm_pool_submit_many + gmm_pool_tick -> masks to pinned host "
+                            "(FP16/BF16 next-tile prefetch off; the launch shape tuned in "
+                            "this pipeline unless fixed)"},
             "e2e_zero_copy": {"value": e2e["zero_copy"], "unit": UNIT,
                               "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                              "launch": e2e["launch_zero_copy"],
                               "path": "gmm_pool_submit_many on the same page-locked tick-sets and "
                                       "masks: the pooled kernel reads frames and writes masks "
                                       "over the host link"},
@@ -972,12 +975,18 @@ def pool_launches(cams, shape):
     return (len(cams) + 127) // 128
 
 
-def run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, steps, warmup, world):
+def run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, steps, warmup, world,
+                 retune=False):
     """Frames from pinned host memory each tick: every camera's frame of a
     tick is packed into one pinned buffer, uploaded with one copy into one of
     two device staging buffers on a copy stream (overlapping the previous
     tick's compute), the pool ticks from there, and the packed masks come back
-    with one copy on a third stream."""
+    with one copy on a third stream, with the pool's FP16/BF16 next-tile
+    prefetch turned off (the library documents that uploads beside each tick
+    slow down under it). Then the zero-copy form, prefetch on. retune: the
+    pool's online tuner runs again inside each of the two pipelines before
+    its warm-up (a shape's tick period then includes what its kernel delays
+    in the uploads beside it, or in its own reads over the host link)."""
     def al(x):
         return (x + 255) // 256 * 256
     off, o = [], 0
@@ -1022,8 +1031,22 @@ def run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, steps, warmup, 
             hmask[k % ring].copy_(dmask[b], non_blocking=True)
             down[b].record(down_s)
 
-    k0 = 0
-    shape = pool.tuning()[1]
+    def tune(step):
+        n = 0
+        if retune:
+            pool.autotune_online(3)
+            while pool.tuning()[0] and n < 2000:
+                step(n)
+                n += 1
+            torch.cuda.synchronize()
+            assert not pool.tuning()[0], "online tuning did not finish"
+        shape = dict(pool.tuning()[1])
+        if retune:
+            shape["tuning_ticks"] = n
+        return n, shape
+
+    pool.set_prefetch(False)
+    k0, shape = tune(tick)
     for k in range(warmup):
         tick(k0 + k)
     torch.cuda.synchronize()
@@ -1046,20 +1069,22 @@ def run_pool_e2e(G, torch, pool, ids, cams, frames, dev, stream, steps, warmup, 
                          [mb_h + r * mask_bytes + m for m in moff])
         pool.tick(stream)
 
+    pool.set_prefetch(True)
+    z0, shape_zc = tune(tick_zc)
     for k in range(warmup):
-        tick_zc(k)
+        tick_zc(z0 + k)
     torch.cuda.synchronize()
     barrier(world, dev)
     t = time.perf_counter()
     for k in range(steps):
-        tick_zc(warmup + k)
+        tick_zc(z0 + warmup + k)
     torch.cuda.synchronize()
     dz = time.perf_counter() - t
     barrier(world, dev)
     dz = reduce_max(dz, world, dev)
     px = sum(H * W for (H, W, _, _) in cams)
     return {"value": world * steps * px / dt / 1e6, "launch": shape,
-            "zero_copy": world * steps * px / dz / 1e6,
+            "zero_copy": world * steps * px / dz / 1e6, "launch_zero_copy": shape_zc,
             "h2d": sum(H * W * 5 for (H, W, _, _) in cams),
             "d2h": sum(H * G.mask_words_per_row(W) * 4 for (H, W, _, _) in cams)}
 

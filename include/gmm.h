@@ -402,6 +402,20 @@ int gmm_pool_set_stream(gmm_pool_t *p, void *cuda_stream);
 int gmm_pool_set_launch(gmm_pool_t *p, int threads, int ctas_per_sm,
                         int tile_pixels);
 
+/* Next-tile prefetch of the FP16/BF16 persistent form (enable = 1, the
+ * default; 0 turns it off). With a launch shape whose tiles hold at most two
+ * pixels per thread, a CTA takes its next tile when the current one starts
+ * (except in the last two waves of a tick's tiles) and prefetches that
+ * tile's first pixels' state into L2. Measured on the 64-camera mix: 94-95%
+ * of the HBM copy bandwidth instead of 90-91% with the frames in device
+ * memory, and no loss with frames read over the host link; but when frames
+ * are uploaded on a copy stream beside each tick, the uploads slow down
+ * (end to end 29 against 36-40 Gpixel-frames/s) and the online tuner's
+ * trial ticks do not show it, so such pipelines should turn it off. It
+ * changes no result (bit for bit the same either way) and does nothing for
+ * FP32 pools. Applies from the next tick. GMM_EINVAL on a null pool. */
+int gmm_pool_set_prefetch(gmm_pool_t *p, int enable);
+
 /* Time each candidate launch shape on the current submissions (the state is
  * snapshotted and restored around the trials, so the models do not move)
  * and keep the fastest. Requires a submitted tick; leaves it submitted.

@@ -126,6 +126,7 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         "gmm_pool_autotune_online": (ctypes.c_int, [_vp, ctypes.c_int]),
         "gmm_pool_tuning": (ctypes.c_int, [_vp] + [ctypes.POINTER(ctypes.c_int)] * 3),
         "gmm_pool_use_graph": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "gmm_pool_set_prefetch": (ctypes.c_int, [_vp, ctypes.c_int]),
         "gmm_pool_state_get": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                               ctypes.c_size_t]),
         "gmm_pool_state_used": (ctypes.c_size_t, [_vp]),
@@ -418,6 +419,11 @@ class Pool:
 
     def use_graph(self, enable=True) -> None:
         _check(load_library().gmm_pool_use_graph(self._p, int(bool(enable))))
+
+    def set_prefetch(self, enable=True) -> None:
+        """FP16/BF16 next-tile L2 prefetch (on by default); turn it off when
+        frames are uploaded on a copy stream beside every tick."""
+        _check(load_library().gmm_pool_set_prefetch(self._p, int(bool(enable))))
 
     def state_get(self, cam, plane, component=0) -> np.ndarray:
         H, W, _ = self.cams[cam]

@@ -76,9 +76,12 @@ static_assert(sizeof(PoolArgs) <= 32768, "one launch's arguments fit half the co
 // that also handles the options and the augmentation alternative; flat: the
 // non-persistent form (tile_begin and n_tiles count one chunk per warp:
 // 32 pixels in FP32, 64 in FP16/BF16; blocks covers every chunk); m: the M
-// every camera of the launch has (a kernel specialised to it), or 0.
+// every camera of the launch has (a kernel specialised to it), or 0;
+// prefetch: the FP16/BF16 persistent instance that takes next tiles early
+// and prefetches them into L2 (else the one that does not).
 cudaError_t launch_pool_tick_impl(const PoolArgs *args_host, int threads, int blocks, int prec,
-                                  bool all_variants, bool flat, int m, cudaStream_t s);
+                                  bool all_variants, bool flat, int m, bool prefetch,
+                                  cudaStream_t s);
 
 // The constant-memory argument bank is shared by every pool on a device:
 // enqueue uploads and launches between acquire (takes the device's lock and

@@ -38,10 +38,11 @@ struct GraphSig {
     int n_launch = -1, threads = 0;
     std::vector<int> blocks; // per launch
     std::vector<int> m; // per launch: the M its cameras share (flat form), else 0
-    bool all_variants = false, flat = false;
+    bool all_variants = false, flat = false, prefetch = true;
     bool operator==(const GraphSig &o) const {
         return n_launch == o.n_launch && threads == o.threads && blocks == o.blocks &&
-               m == o.m && all_variants == o.all_variants && flat == o.flat;
+               m == o.m && all_variants == o.all_variants && flat == o.flat &&
+               prefetch == o.prefetch;
     }
 };
 
@@ -105,6 +106,7 @@ struct gmm_pool {
     bool staged_used[kStaging] = {};
     int buf = 0;
     bool use_graph = false;
+    bool prefetch = true; // FP16/BF16: next-tile L2 prefetch in the persistent form
     cudaGraphExec_t gexec[kStaging] = {};
     GraphSig gsig[kStaging];
     Tuning tune;
@@ -226,7 +228,8 @@ static cudaError_t enqueue_body(gmm_pool *p, cudaStream_t s, int b, const GraphS
     cudaError_t e = cudaSuccess;
     for (int li = 0; li < sig.n_launch && e == cudaSuccess; ++li)
         e = gmmhost::launch_pool_tick_impl(&p->h_args[b][li], sig.threads, sig.blocks[li],
-                                           p->prec, sig.all_variants, sig.flat, sig.m[li], s);
+                                           p->prec, sig.all_variants, sig.flat, sig.m[li],
+                                           sig.prefetch, s);
     return e;
 }
 
@@ -238,6 +241,7 @@ static cudaError_t launch_tick(gmm_pool *p, int b, int n_launch, bool all_varian
     sig.threads = p->threads;
     sig.all_variants = all_variants;
     sig.flat = p->ctas_per_sm < 0;
+    sig.prefetch = p->prefetch;
     const int warps = p->threads / 32;
     for (int li = 0; li < n_launch; ++li) { // flat: one warp per chunk
         sig.blocks.push_back(sig.flat ? (int)((p->h_args[b][li].n_tiles + warps - 1) / warps)
@@ -596,6 +600,13 @@ int gmm_pool_set_launch(gmm_pool_t *p, int threads, int ctas_per_sm, int tile_pi
     p->threads = t;
     p->ctas_per_sm = c;
     p->tile_pixels = tp;
+    return GMM_OK;
+}
+
+int gmm_pool_set_prefetch(gmm_pool_t *p, int enable) {
+    if (!p)
+        return fail(GMM_EINVAL, "gmm_pool_set_prefetch: null pool");
+    p->prefetch = enable != 0; // picks the kernel instance from the next tick
     return GMM_OK;
 }
 

@@ -111,7 +111,8 @@ __device__ __forceinline__ void take_next(const PoolArgs &a, int64_t *s_tile, in
 // instance that also handles the options, which keeps room to avoid spills.
 // FP32 state, and the instance that also handles the options: thread 0
 // takes a tile from the counter and publishes it between two barriers.
-// FP16/BF16 state (kPrefetch): a CTA's current and next tile (and camera) sit
+// FP16/BF16 state (kPrefetch; kPF = false is the instance for pools that
+// turned the prefetch off): a CTA's current and next tile (and camera) sit
 // in alternate slots; thread 0 takes the next tile at the end of the current
 // one, or, for tiles of at most two pixels per thread while at least two
 // waves of tiles remain beyond the current one, at its start, and then
@@ -123,9 +124,9 @@ __device__ __forceinline__ void take_next(const PoolArgs &a, int64_t *s_tile, in
 // (HBM-bound), prefetching measured slower. One barrier per tile; slot k ^ 1
 // is written only after the barrier that ended the tile at whose start every
 // thread last read it.
-template <int PREC, bool kAll>
+template <int PREC, bool kAll, bool kPF = true>
 __global__ void __launch_bounds__(256, (PREC == 0 && kAll) ? 3 : 4) k_pool_tick() {
-    constexpr bool kPrefetch = PREC != 0 && !kAll;
+    constexpr bool kPrefetch = PREC != 0 && !kAll && kPF;
     const PoolArgs &a = c_pool;
     __shared__ int64_t s_tile[2];
     __shared__ int s_job[2];
@@ -299,7 +300,8 @@ cudaError_t pool_bank_release(int device, cudaStream_t s) {
 }
 
 cudaError_t launch_pool_tick_impl(const PoolArgs *args_host, int threads, int blocks, int prec,
-                                  bool all_variants, bool flat, int m, cudaStream_t s) {
+                                  bool all_variants, bool flat, int m, bool prefetch,
+                                  cudaStream_t s) {
     cudaError_t e = cudaMemcpyToSymbolAsync(c_pool, args_host, sizeof(PoolArgs), 0,
                                             cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess)
@@ -317,8 +319,10 @@ cudaError_t launch_pool_tick_impl(const PoolArgs *args_host, int threads, int bl
         k_pool_tick<0, false><<<blocks, threads, 0, s>>>();
     else if (prec == 0)
         k_pool_tick<0, true><<<blocks, threads, 0, s>>>();
-    else if (!all_variants)
+    else if (!all_variants && prefetch)
         k_pool_tick<1, false><<<blocks, threads, 0, s>>>();
+    else if (!all_variants)
+        k_pool_tick<1, false, false><<<blocks, threads, 0, s>>>();
     else
         k_pool_tick<1, true><<<blocks, threads, 0, s>>>();
     return cudaGetLastError();

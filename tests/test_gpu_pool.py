@@ -34,9 +34,11 @@ def _alone(frames, schedule, precision=G.PREC_F32):
     return out
 
 
-def _pooled(frames, schedule, graph=False, launch=None, precision=G.PREC_F32, online=0):
+def _pooled(frames, schedule, graph=False, launch=None, precision=G.PREC_F32, online=0,
+            prefetch=True):
     import torch
     pool = G.Pool(precision=precision, max_cams=8)
+    pool.set_prefetch(prefetch)
     if graph:
         pool.use_graph(True)
     if launch:
@@ -292,3 +294,21 @@ def test_two_pools_on_two_streams():
         for i in halves[h]:
             assert np.array_equal(pools[h].planes(ids[h][i]), a[i]), i
         pools[h].close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_pool_fp16_prefetch_changes_nothing_but_speed(graph):
+    """FP16/BF16 pool with tiles of one pixel per thread and one CTA per SM,
+    so a tick has more than two waves of tiles and CTAs take their next tile
+    early and prefetch it: masks and state equal each camera run alone, and
+    the pool with the prefetch turned off, bit for bit, on every tick."""
+    n = 6
+    frames = _frames(n)
+    schedule = [set(range(len(CAMS)))] * n
+    a = _alone(frames, schedule, precision=G.PREC_F16)
+    on, _, _ = _pooled(frames, schedule, graph=graph, launch=(64, 1, 64), precision=G.PREC_F16)
+    off, _, _ = _pooled(frames, schedule, graph=graph, launch=(64, 1, 64), precision=G.PREC_F16,
+                        prefetch=False)
+    for key in a:
+        assert np.array_equal(a[key], on[key]), key
+        assert np.array_equal(off[key], on[key]), key

@@ -108,3 +108,21 @@ def test_pool_launch_count():
     assert bench.pool_launches(cams, {"ctas_per_sm": -1}) == len(ms)
     many = cams * 3  # 192 cameras: two launches of up to 128
     assert bench.pool_launches(many, None) == 2
+
+
+def test_committed_captures_match_the_kernel_sources():
+    """The ncu summaries under profiles/ that the bench quotes DRAM traffic
+    from were taken on the kernel sources as they stand: the single-camera
+    ticks (FP32 and FP16/BF16), the pooled tick's small case in both
+    precisions, and the full 64-camera launch of the default workloads (c2,
+    and its cameras with FP16/BF16 state), whose algorithmic bytes must be
+    exactly those of that launch."""
+    cams = bench.camera_mix(16, 0)
+    full = {p: sum(H * W * bench.bytes_per_pixel(M, p) for (H, W, M, _) in cams) for p in (0, 1)}
+    assert full[0] == 15622348800.0 and full[1] == 8003788800.0
+    for p in (0, 1):
+        assert bench.recorded_traffic("tick", p, 1.0) is not None, p
+        assert bench.recorded_traffic("pool", p, 1.0) is not None, p
+        t = bench.recorded_traffic("pool_full", p, full[p], exact=True)
+        # a capture of the whole launch: DRAM bytes within 1% of the algorithmic bytes
+        assert t is not None and abs(t / full[p] - 1.0) < 0.01, (p, t)

@@ -4,10 +4,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <utility>
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "gmm.h"

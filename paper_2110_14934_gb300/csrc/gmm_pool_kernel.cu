@@ -109,10 +109,10 @@ __device__ __forceinline__ void take_next(const PoolArgs &a, int64_t *s_tile, in
 // Registers: 64 in both precisions (32 resident warps per SM; FP32 at 72,
 // 28 warps, measured 0.8% slower on the 64-camera mix), except the FP32
 // instance that also handles the options, which keeps room to avoid spills.
-// FP32 state, and the instance that also handles the options: thread 0
-// takes a tile from the counter and publishes it between two barriers.
-// FP16/BF16 state (kPrefetch; kPF = false is the instance for pools that
-// turned the prefetch off): a CTA's current and next tile (and camera) sit
+// FP32 state, the instance that also handles the options, and FP16/BF16
+// pools that turned the prefetch off (kPF = false): thread 0 takes a tile
+// from the counter and publishes it between two barriers. Otherwise, in
+// FP16/BF16 state (kPrefetch): a CTA's current and next tile (and camera) sit
 // in alternate slots; thread 0 takes the next tile at the end of the current
 // one, or, for tiles of at most two pixels per thread while at least two
 // waves of tiles remain beyond the current one, at its start, and then
